@@ -1,0 +1,202 @@
+/*
+ * founsure_gpu.h - C ABI of the GB300 (sm_103a) Founsure gather-XOR library.
+ *
+ * Operations follow Arslan, "Founsure 1.0: An Erasure Code Library with
+ * Efficient Repair and Update Features" (arXiv 1702.07409):
+ *   encode  - Section 2.2: (1) precode parities (check #1), then (2) each of
+ *             n coded blocks is the XOR (region XOR, Section 2.2) of its
+ *             LDGM neighbours among the k_int = b + m intermediates.
+ *   decode  - Algorithm 5 (Decoding Path Generation, Section 3.2) with the
+ *             two rules of Section 3.1, then the payload of that path.
+ *   repair  - Section 4 "conventional repair": a lost coded block is
+ *             recomputed from the intermediates by the encoding rule.
+ *   update  - data rewrite propagated by linearity: old XOR new of each
+ *             rewritten block is XORed into every parity and coded block that
+ *             has it as a neighbour (the paper's own "update", Section 2.9,
+ *             generates extra coded rows, which is fs_encode_rows).
+ *
+ * Notation: b data blocks, m precode parities, k_int = b + m, n coded blocks,
+ * t = block_bytes. Intermediate v is data block v for v < b and parity v - b
+ * otherwise. Every payload buffer is block-major: block i occupies bytes
+ * [i*t, (i+1)*t) of one contiguous buffer. t must be a positive multiple of
+ * 16 and every device pointer 16-byte aligned.
+ *
+ * Ownership: the caller owns every device buffer (payloads, flags, index
+ * lists, workspaces) and the stream. The library owns the fs_code object and
+ * the device copies of its graphs, allocated once by fs_code_create.
+ * Hot calls (fs_encode ... fs_update) allocate nothing: scratch comes from the
+ * caller's workspace, sized by fs_workspace_bytes.
+ *
+ * Asynchrony and errors: every hot call only enqueues work on `stream` and
+ * returns. Its return value covers host-side argument checks and launch
+ * errors (FS_ERR_INVALID, FS_ERR_CUDA). Conditions found on the device (an
+ * index out of range, a repeated update index, a bounded wait that gave up)
+ * are written to the workspace status word (int32 at byte offset
+ * FS_WS_STATUS_OFFSET of d_ws) as an fs_status value; it reads FS_OK after a
+ * clean call. Decode stalls are results, not errors: the count of
+ * unrecovered intermediates is written to *d_n_unrecovered. No call aborts
+ * or traps.
+ */
+#ifndef FOUNSURE_GPU_H
+#define FOUNSURE_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FS_OK = 0,
+    FS_STALL = 1,       /* decode finished with unrecovered intermediates */
+    FS_ERR_INVALID = 2, /* bad argument, graph, alignment or index */
+    FS_ERR_CUDA = 3,    /* a CUDA runtime call failed */
+    FS_ERR_NOMEM = 4,   /* fs_code_create could not allocate */
+    FS_ERR_TIMEOUT = 5  /* a bounded device wait gave up */
+} fs_status;
+
+/* A bipartite graph in CSR form, in HOST memory. Row r lists column indices
+ * col_idx[row_ptr[r] .. row_ptr[r+1]) in strictly ascending order, each in
+ * [0, n_cols). row_ptr has n_rows + 1 entries, row_ptr[0] == 0. */
+typedef struct {
+    int32_t n_rows;
+    int32_t n_cols;
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+} fs_csr;
+
+typedef struct fs_code fs_code; /* opaque; owned by the library */
+
+/* flags for fs_code_create (decoding mode, Section 2.2 / Algorithm 5) */
+#define FS_DECODE_JOINT    0 /* peel coded rows and precode checks together */
+#define FS_DECODE_TWO_PASS 1 /* peel coded rows to a fixpoint, then checks */
+
+/* op codes for fs_workspace_bytes */
+#define FS_OP_ENCODE 0
+#define FS_OP_DECODE 1
+#define FS_OP_UPDATE 2
+#define FS_OP_REPAIR 3
+
+#define FS_WS_STATUS_OFFSET 0 /* int32 device status word inside every workspace */
+
+/*
+ * Creates a code from its two graphs (Section 2.2, Figure 2):
+ *   precode: m rows (checks) over n_cols = b data blocks, or NULL for m = 0;
+ *   lt:      n rows (coded blocks) over n_cols = k_int = b + m intermediates.
+ * With precode == NULL, b is taken as lt->n_cols. block_bytes = t.
+ * Validates both graphs on the host (bounds, ascending rows, sizes; empty
+ * rows are allowed), builds the joint constraint graph and its transpose and
+ * copies them to the current device. Returns FS_ERR_INVALID on a bad graph,
+ * FS_ERR_NOMEM / FS_ERR_CUDA on allocation or copy failure. *out is set only
+ * on FS_OK. Synchronous; not a hot call.
+ */
+fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t block_bytes,
+                         int flags, fs_code **out);
+/* Frees the device graphs of the code (synchronises the device). NULL is a no-op. */
+void fs_code_destroy(fs_code *code);
+/* Sizes of the code: any out pointer may be NULL. */
+fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
+                       size_t *block_bytes);
+
+/* Bytes of caller-provided device workspace that op needs. n_items is the
+ * largest n_idx an FS_OP_UPDATE call will pass (ignored for other ops).
+ * Workspaces are 256-byte aligned by the caller; one workspace must not be
+ * used by two calls that may overlap on the device. */
+size_t fs_workspace_bytes(const fs_code *code, int op, int32_t n_items);
+
+/*
+ * Encode (Section 2.2, steps (1) and (2)).
+ *   d_data   [b*t]  input, read only
+ *   d_parity [m*t]  output parities (NULL iff m == 0)
+ *   d_coded  [n*t]  output coded blocks
+ *   d_ws     FS_OP_ENCODE workspace
+ */
+fs_status fs_encode(const fs_code *code, const void *d_data, void *d_parity, void *d_coded,
+                    void *d_ws, void *stream);
+
+/*
+ * Encode only coded rows [row_begin, row_end) (the paper's update by code
+ * extension, Section 2.9, when the LT graph was drawn with extra rows), from
+ * resident intermediates d_data / d_parity. Writes rows row_begin..row_end-1
+ * of d_coded (block-major over all n rows).
+ */
+fs_status fs_encode_rows(const fs_code *code, int32_t row_begin, int32_t row_end,
+                         const void *d_data, const void *d_parity, void *d_coded, void *d_ws,
+                         void *stream);
+
+/*
+ * Decode (Algorithm 5 + payload, Section 3.1 / 3.2).
+ *   d_coded         [n*t]   received coded blocks; erased rows are ignored
+ *   d_erased        [n]     uint8 flags, nonzero = coded block j erased
+ *   d_data_out      [b*t]   recovered data; unrecovered blocks are zero
+ *   d_unrecovered   [k_int] uint8 flags, 1 = intermediate not recovered
+ *   d_n_unrecovered [1]     int32 count of unrecovered intermediates
+ *   d_ws            FS_OP_DECODE workspace; also holds the parity
+ *                   intermediates and the decoding path afterwards
+ * Mode (joint / two-pass) comes from the code's flags.
+ */
+fs_status fs_decode(const fs_code *code, const void *d_coded, const uint8_t *d_erased,
+                    void *d_data_out, uint8_t *d_unrecovered, int32_t *d_n_unrecovered,
+                    void *d_ws, void *stream);
+
+/*
+ * The two halves of fs_decode, for callers that reuse one decoding path over
+ * many stripes that share a graph and an erasure pattern (Section 2.2:
+ * partitions of a file are coded with the same graph; a failed disk erases
+ * the same rows of each):
+ *   fs_decode_schedule - Algorithm 5 only: writes the path into d_ws and the
+ *                        unrecovered flags / count (arguments as fs_decode);
+ *   fs_decode_payload  - the payload of the path held in d_ws: reads d_coded,
+ *                        writes d_data_out (unrecovered blocks zero) and the
+ *                        parity intermediates inside d_ws.
+ * fs_decode(...) is fs_decode_schedule followed by fs_decode_payload.
+ */
+fs_status fs_decode_schedule(const fs_code *code, const uint8_t *d_erased, uint8_t *d_unrecovered,
+                             int32_t *d_n_unrecovered, void *d_ws, void *stream);
+fs_status fs_decode_payload(const fs_code *code, const void *d_coded, void *d_data_out,
+                            void *d_ws, void *stream);
+
+/* Device pointers into a decode workspace, valid after fs_decode completes:
+ * the decoding path DP of Algorithm 5 as pairs (pair_f[p], pair_g[p]) for
+ * p < *n_pairs, level l owning pairs [level_off[l], level_off[l+1]) for
+ * l < *n_levels. Inside a level the pair order is unspecified. Constraint g
+ * is coded row g for g < n and precode check g - n otherwise. */
+typedef struct {
+    const int32_t *n_levels;  /* device int32 */
+    const int32_t *n_pairs;   /* device int32 */
+    const int32_t *level_off; /* device int32[k_int + 2] */
+    const int32_t *pair_f;    /* device int32[k_int] */
+    const int32_t *pair_g;    /* device int32[k_int] */
+    const uint8_t *parity;    /* device [m*t]: recovered parity intermediates */
+} fs_path_view;
+fs_status fs_decode_path(const fs_code *code, const void *d_ws, fs_path_view *out);
+
+/*
+ * Update: data blocks d_idx[q] (q < n_idx, distinct, each < b) are replaced
+ * by d_new[q*t .. (q+1)*t). For each one, delta = old XOR new is XORed into
+ * every parity whose check contains it and every coded block whose
+ * neighbours contain it or a changed parity, so that afterwards d_parity and
+ * d_coded equal a full re-encode of the new data. d_data is updated in place.
+ * A repeated or out-of-range index sets FS_ERR_INVALID in the workspace
+ * status word. n_idx == 0 is a no-op.
+ */
+fs_status fs_update(const fs_code *code, const int32_t *d_idx, int32_t n_idx, const void *d_new,
+                    void *d_data, void *d_parity, void *d_coded, void *d_ws, void *stream);
+
+/*
+ * Repair (conventional repair, Section 4): each lost coded block d_lost[q]
+ * (q < n_lost, each < n) is recomputed from the resident intermediates
+ * d_data / d_parity into its place in d_coded. An out-of-range index sets
+ * FS_ERR_INVALID in the workspace status word and is skipped.
+ */
+fs_status fs_repair(const fs_code *code, const int32_t *d_lost, int32_t n_lost, const void *d_data,
+                    const void *d_parity, void *d_coded, void *d_ws, void *stream);
+
+/* Static string naming a status. */
+const char *fs_status_string(fs_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,122 @@
+// fs_internal.cuh - internal definitions shared by the translation units of
+// libfounsure_gpu.so (code object, workspace layout, kernel launchers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "founsure_gpu.h"
+
+#define FS_API extern "C" __attribute__((visibility("default")))
+
+// Joint constraint graph of a code (Algorithm 5 over coded rows and precode
+// checks): constraint g < n is coded row g with payload c_g; constraint
+// n + j is precode check j with payload zero and vars = members + {b + j}.
+// The LT graph is the prefix con_ptr[0..n], con_idx[0..e_lt).
+struct fs_code {
+    int32_t b, m, n, k_int, n_con;
+    int64_t t;            // block bytes
+    int64_t tw;           // block size in 16-byte words
+    int flags;
+    int64_t e_lt, e_pre, e_con;
+    int32_t max_con_deg;  // largest constraint degree
+    int32_t max_var_deg;  // largest number of constraints containing one var
+    // device arrays
+    int32_t *con_ptr;     // [n_con + 1]
+    int32_t *con_idx;     // [e_con]
+    int32_t *pre_ptr;     // [m + 1]   precode rows (members only)
+    int32_t *pre_idx;     // [e_pre]
+    int32_t *var_ptr;     // [k_int + 1] transpose of the joint graph
+    int32_t *var_idx;     // [e_con]
+    int device;
+    int num_sms;
+    size_t smem_optin;    // max dynamic shared memory per block
+};
+
+// ---- workspace layouts (byte offsets from d_ws, 256-aligned) --------------
+static inline size_t fs_align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// header words (int32) at the start of every workspace
+enum {
+    WS_STATUS = 0,      // fs_status of the last call (device side)
+    WS_N_LEVELS = 1,
+    WS_N_PAIRS = 2,
+    WS_N_UNREC_DATA = 3,
+    WS_COUNT_A = 4,     // scratch counters
+    WS_COUNT_B = 5,
+    WS_TILE_CTR = 6,
+    WS_HDR_BYTES = 256
+};
+
+struct DecodeLayout {
+    size_t res, best, known, front_a, front_b, touched, pair_f, pair_g, level_off,
+        recipe_off, recipe_h, unrec_list, parity, total;
+};
+
+static inline DecodeLayout decode_layout(const fs_code *c) {
+    DecodeLayout L;
+    size_t o = WS_HDR_BYTES;
+    size_t K = (size_t)c->k_int, G = (size_t)c->n_con;
+    L.res = o;        o = fs_align256(o + 4 * (G + 1));
+    L.best = o;       o = fs_align256(o + 8 * (K + 1));
+    L.known = o;      o = fs_align256(o + (K + 1));
+    L.front_a = o;    o = fs_align256(o + 4 * (G + 1));
+    L.front_b = o;    o = fs_align256(o + 4 * (G + 1));
+    L.touched = o;    o = fs_align256(o + 4 * (K + 1));
+    L.pair_f = o;     o = fs_align256(o + 4 * (K + 1));
+    L.pair_g = o;     o = fs_align256(o + 4 * (K + 1));
+    L.level_off = o;  o = fs_align256(o + 4 * (K + 2));
+    L.recipe_off = o; o = fs_align256(o + 4 * (K + 1));
+    L.recipe_h = o;   o = fs_align256(o + 4 * ((size_t)c->e_con + 1));
+    L.unrec_list = o; o = fs_align256(o + 4 * (K + 1));
+    L.parity = o;     o = fs_align256(o + (size_t)c->m * (size_t)c->t);
+    L.total = o;
+    return L;
+}
+
+struct UpdateLayout {
+    size_t mark, pmark, delta, pdelta, total;
+};
+
+static inline UpdateLayout update_layout(const fs_code *c, int32_t n_items) {
+    UpdateLayout L;
+    size_t o = WS_HDR_BYTES;
+    L.mark = o;   o = fs_align256(o + 4 * ((size_t)c->b + 1));
+    L.pmark = o;  o = fs_align256(o + 4 * ((size_t)c->m + 1));
+    L.delta = o;  o = fs_align256(o + (size_t)(n_items > 0 ? n_items : 0) * (size_t)c->t);
+    L.pdelta = o; o = fs_align256(o + (size_t)c->m * (size_t)c->t);
+    L.total = o;
+    return L;
+}
+
+// ---- kernel launchers (return cudaError_t of the launch) ----------------
+// Gather-XOR over CSR rows: out row r = XOR of input blocks idx[ptr[r]..ptr[r+1]).
+// Input block v lives at inA + v*tw (v < split) or inB + (v - split)*tw.
+// rows == nullptr: row r writes out + r*tw; else it processes CSR row rows[r]
+// (checked against n_valid) and writes out + rows[r]*tw.
+struct GatherArgs {
+    const int32_t *ptr;
+    const int32_t *idx;
+    const int32_t *rows;
+    int32_t n_rows;
+    int32_t row_base;    // added to r when rows == nullptr
+    int32_t n_valid;     // bound for rows[r]
+    const uint4 *inA;
+    const uint4 *inB;
+    int32_t split;
+    uint4 *out;
+    int64_t tw;
+    int32_t *status;
+};
+cudaError_t launch_gather(const GatherArgs &a, int num_sms, cudaStream_t s);
+
+// Decoding path generation (Algorithm 5), one CTA.
+cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws,
+                       uint8_t *unrecovered, int32_t *n_unrecovered, cudaStream_t s);
+// Payload of the decoding path.
+cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_t *ws,
+                        cudaStream_t s);
+
+// Update kernels.
+cudaError_t launch_update(const fs_code *c, const int32_t *idx, int32_t n_idx, const uint4 *d_new,
+                          uint4 *data, uint4 *parity, uint4 *coded, uint8_t *ws, cudaStream_t s);

@@ -1,0 +1,246 @@
+"""Python binding of ``libfounsure_gpu.so`` (the C ABI in include/founsure_gpu.h).
+
+Argument marshalling only: every step of encode, decode, update and repair
+runs in the library's CUDA kernels. PyTorch supplies device memory and
+streams; buffers are passed as ``torch.Tensor`` (CUDA, contiguous) or as raw
+device addresses (``int``). There is no CPU fallback: if the library cannot
+be built or loaded, or no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+FS_OK, FS_STALL, FS_ERR_INVALID, FS_ERR_CUDA, FS_ERR_NOMEM, FS_ERR_TIMEOUT = range(6)
+DECODE_JOINT, DECODE_TWO_PASS = 0, 1
+OP_ENCODE, OP_DECODE, OP_UPDATE, OP_REPAIR = 0, 1, 2, 3
+WS_STATUS_OFFSET = 0
+
+#: every symbol declared in include/founsure_gpu.h
+EXPORTS = ("fs_code_create", "fs_code_destroy", "fs_code_info", "fs_workspace_bytes",
+           "fs_encode", "fs_encode_rows", "fs_decode", "fs_decode_schedule",
+           "fs_decode_payload", "fs_decode_path", "fs_update", "fs_repair", "fs_status_string")
+
+
+class FounsureError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s: %s" % (what, status_string(status)))
+        self.status = status
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int32), ("n_cols", ctypes.c_int32),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p)]
+
+
+class _PathView(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_void_p), ("n_pairs", ctypes.c_void_p),
+                ("level_off", ctypes.c_void_p), ("pair_f", ctypes.c_void_p),
+                ("pair_g", ctypes.c_void_p), ("parity", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads (building if stale) the CUDA library. Raises if it cannot."""
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(_build.build_gpu())
+        vp, i32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+        L.fs_code_create.argtypes = [vp, vp, sz, ctypes.c_int, ctypes.POINTER(vp)]
+        L.fs_code_create.restype = ctypes.c_int
+        L.fs_code_destroy.argtypes = [vp]
+        L.fs_code_destroy.restype = None
+        L.fs_code_info.argtypes = [vp, vp, vp, vp, vp]
+        L.fs_code_info.restype = ctypes.c_int
+        L.fs_workspace_bytes.argtypes = [vp, ctypes.c_int, i32]
+        L.fs_workspace_bytes.restype = sz
+        L.fs_encode.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.fs_encode.restype = ctypes.c_int
+        L.fs_encode_rows.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
+        L.fs_encode_rows.restype = ctypes.c_int
+        L.fs_decode.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.fs_decode.restype = ctypes.c_int
+        L.fs_decode_schedule.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.fs_decode_schedule.restype = ctypes.c_int
+        L.fs_decode_payload.argtypes = [vp, vp, vp, vp, vp]
+        L.fs_decode_payload.restype = ctypes.c_int
+        L.fs_decode_path.argtypes = [vp, vp, ctypes.POINTER(_PathView)]
+        L.fs_decode_path.restype = ctypes.c_int
+        L.fs_update.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp, vp]
+        L.fs_update.restype = ctypes.c_int
+        L.fs_repair.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
+        L.fs_repair.restype = ctypes.c_int
+        L.fs_status_string.argtypes = [ctypes.c_int]
+        L.fs_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().fs_status_string(int(s)).decode()
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != FS_OK:
+        raise FounsureError(rc, what)
+
+
+def _addr(x) -> Optional[int]:
+    """Device address of a CUDA tensor (or an int address, or None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return x.data_ptr()
+
+
+def _nbytes(x) -> int:
+    return x.numel() * x.element_size()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Code:
+    """A Founsure code on the current CUDA device (fs_code_create).
+
+    ``graph`` is any object with b, m, n, pre_ptr, pre_idx, lt_ptr, lt_idx
+    (e.g. ``gen.Graph``); ``block_bytes`` is t (a multiple of 16)."""
+
+    def __init__(self, graph, block_bytes: int, mode: int = DECODE_JOINT):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the Founsure GPU library has no CPU path")
+        self.b, self.m, self.n = int(graph.b), int(graph.m), int(graph.n)
+        self.k_int = self.b + self.m
+        self.t = int(block_bytes)
+        self.mode = mode
+        self._keep = []
+        pre = None
+        if self.m > 0:
+            pp = np.ascontiguousarray(graph.pre_ptr, np.int32)
+            pi = np.ascontiguousarray(graph.pre_idx, np.int32)
+            self._keep += [pp, pi]
+            pre = _Csr(self.m, self.b, pp.ctypes.data, pi.ctypes.data if pi.size else None)
+        lp = np.ascontiguousarray(graph.lt_ptr, np.int32)
+        li = np.ascontiguousarray(graph.lt_idx, np.int32)
+        self._keep += [lp, li]
+        lt = _Csr(self.n, self.k_int, lp.ctypes.data, li.ctypes.data if li.size else None)
+        h = ctypes.c_void_p()
+        rc = lib().fs_code_create(ctypes.byref(pre) if pre is not None else None,
+                                  ctypes.byref(lt), self.t, mode, ctypes.byref(h))
+        _check(rc, "fs_code_create")
+        self._h = h
+        self._lib = lib()
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.fs_code_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- workspaces -----------------------------------------------------------
+    def workspace_bytes(self, op: int, n_items: int = 0) -> int:
+        return int(lib().fs_workspace_bytes(self._h, op, n_items))
+
+    def workspace(self, op: int, n_items: int = 0, device=None):
+        import torch
+        return torch.empty(max(self.workspace_bytes(op, n_items), 256), dtype=torch.uint8,
+                           device=device or "cuda")
+
+    @staticmethod
+    def ws_status(ws) -> int:
+        """Device status word of a workspace (synchronises the device)."""
+        import torch
+        torch.cuda.synchronize()
+        return int(ws[WS_STATUS_OFFSET:WS_STATUS_OFFSET + 4].view(torch.int32).item())
+
+    # -- operations -----------------------------------------------------------
+    def _need(self, x, nbytes, name):
+        if x is not None and not isinstance(x, int) and _nbytes(x) < nbytes:
+            raise ValueError("%s holds %d bytes, needs %d" % (name, _nbytes(x), nbytes))
+
+    def encode(self, data, parity, coded, ws, stream=None) -> None:
+        self._need(data, self.b * self.t, "data")
+        self._need(parity, self.m * self.t, "parity")
+        self._need(coded, self.n * self.t, "coded")
+        _check(lib().fs_encode(self._h, _addr(data), _addr(parity), _addr(coded), _addr(ws),
+                               _stream(stream)), "fs_encode")
+
+    def encode_rows(self, row_begin, row_end, data, parity, coded, ws, stream=None) -> None:
+        _check(lib().fs_encode_rows(self._h, row_begin, row_end, _addr(data), _addr(parity),
+                                    _addr(coded), _addr(ws), _stream(stream)), "fs_encode_rows")
+
+    def decode(self, coded, erased, data_out, unrecovered, n_unrecovered, ws, stream=None) -> None:
+        self._need(coded, self.n * self.t, "coded")
+        self._need(erased, self.n, "erased")
+        self._need(data_out, self.b * self.t, "data_out")
+        self._need(unrecovered, self.k_int, "unrecovered")
+        self._need(ws, self.workspace_bytes(OP_DECODE), "ws")
+        _check(lib().fs_decode(self._h, _addr(coded), _addr(erased), _addr(data_out),
+                               _addr(unrecovered), _addr(n_unrecovered), _addr(ws),
+                               _stream(stream)), "fs_decode")
+
+    def decode_schedule(self, erased, unrecovered, n_unrecovered, ws, stream=None) -> None:
+        self._need(ws, self.workspace_bytes(OP_DECODE), "ws")
+        _check(lib().fs_decode_schedule(self._h, _addr(erased), _addr(unrecovered),
+                                        _addr(n_unrecovered), _addr(ws), _stream(stream)),
+               "fs_decode_schedule")
+
+    def decode_payload(self, coded, data_out, ws, stream=None) -> None:
+        self._need(data_out, self.b * self.t, "data_out")
+        _check(lib().fs_decode_payload(self._h, _addr(coded), _addr(data_out), _addr(ws),
+                                       _stream(stream)), "fs_decode_payload")
+
+    def decode_path(self, ws):
+        """Views into a decode workspace after fs_decode (synchronises):
+        returns dict(n_levels, n_pairs, level_off, pair_f, pair_g, parity)."""
+        import torch
+        v = _PathView()
+        _check(lib().fs_decode_path(self._h, _addr(ws), ctypes.byref(v)), "fs_decode_path")
+        base = ws.data_ptr()
+
+        def at(ptr, count, dtype):
+            off = ptr - base
+            esz = torch.tensor([], dtype=dtype).element_size()
+            return ws[off:off + count * esz].view(dtype)
+
+        torch.cuda.synchronize()
+        nl = int(at(v.n_levels, 1, torch.int32).item())
+        npairs = int(at(v.n_pairs, 1, torch.int32).item())
+        return dict(n_levels=nl, n_pairs=npairs,
+                    level_off=at(v.level_off, nl + 1, torch.int32),
+                    pair_f=at(v.pair_f, npairs, torch.int32),
+                    pair_g=at(v.pair_g, npairs, torch.int32),
+                    parity=at(v.parity, self.m * self.t, torch.uint8))
+
+    def update(self, idx, n_idx: int, new, data, parity, coded, ws, stream=None) -> None:
+        self._need(new, n_idx * self.t, "new")
+        self._need(ws, self.workspace_bytes(OP_UPDATE, n_idx), "ws")
+        _check(lib().fs_update(self._h, _addr(idx), n_idx, _addr(new), _addr(data), _addr(parity),
+                               _addr(coded), _addr(ws), _stream(stream)), "fs_update")
+
+    def repair(self, lost, n_lost: int, data, parity, coded, ws, stream=None) -> None:
+        _check(lib().fs_repair(self._h, _addr(lost), n_lost, _addr(data), _addr(parity),
+                               _addr(coded), _addr(ws), _stream(stream)), "fs_repair")

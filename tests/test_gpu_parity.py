@@ -1,0 +1,230 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle, bit for
+bit: coded and parity bytes, recovered data, unrecovered flags and counts,
+the per-level decoding path (Algorithm 5) and device status words."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1702_07409_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+
+def _fs():
+    from paper_1702_07409_gb300 import founsure
+    return founsure
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _host(x):
+    return x.cpu().numpy()
+
+
+def _erased(n, frac, seed):
+    e = np.zeros(n, np.uint8)
+    e[gen.sample_indices(n, gen.round_count(frac, n), seed)] = 1
+    return e
+
+
+class Case:
+    def __init__(self, b, m, n, t, dist, c=0.0, delta=0.0, seed_data=gen.SEED_DATA, stripe=0,
+                 mode=0):
+        self.g = gen.make_graph(b, m, n, dist, c, delta, stripe=stripe)
+        self.b, self.m, self.n, self.t = b, m, n, t
+        self.data = gen.fill_bytes(seed_data + (stripe << gen.STRIPE_SHIFT), b * t).reshape(b, t)
+        self.code = _fs().Code(self.g, t, mode)
+        self.mode = mode
+
+    def encode_gpu(self):
+        import torch
+        d = _dev(self.data)
+        p = torch.empty((self.m, self.t), dtype=torch.uint8, device="cuda") if self.m else None
+        cd = torch.empty((self.n, self.t), dtype=torch.uint8, device="cuda")
+        ws = self.code.workspace(_fs().OP_ENCODE)
+        self.code.encode(d, p, cd, ws)
+        torch.cuda.synchronize()
+        return d, p, cd
+
+    def decode_gpu(self, coded_dev, erased):
+        import torch
+        out = torch.full((self.b, self.t), 0xA5, dtype=torch.uint8, device="cuda")
+        unrec = torch.empty(self.b + self.m, dtype=torch.uint8, device="cuda")
+        nun = torch.empty(1, dtype=torch.int32, device="cuda")
+        ws = self.code.workspace(_fs().OP_DECODE)
+        self.code.decode(coded_dev, _dev(erased), out, unrec, nun, ws)
+        torch.cuda.synchronize()
+        return out, unrec, nun, ws
+
+
+def _path_levels(view):
+    lo = _host(view["level_off"])
+    f = _host(view["pair_f"])
+    g = _host(view["pair_g"])
+    return [set(zip(f[lo[l]:lo[l + 1]].tolist(), g[lo[l]:lo[l + 1]].tolist()))
+            for l in range(view["n_levels"])]
+
+
+def _check_decode(case, coded_np, coded_dev, erased):
+    out, unrec, nun, ws = case.decode_gpu(coded_dev, erased)
+    want, path = oracle.decode(case.g, coded_np, erased, case.t, case.mode)
+    assert np.array_equal(_host(unrec), path.unrecovered)
+    assert int(_host(nun)[0]) == int(path.unrecovered.sum())
+    assert np.array_equal(_host(out), want)
+    view = case.code.decode_path(ws)
+    assert view["n_levels"] == path.n_levels and view["n_pairs"] == path.n_pairs
+    assert _path_levels(view) == path.levels()
+    if case.m:
+        _, par = oracle.peel(case.g, coded_np, path, case.t, with_parity=True)
+        got = _host(view["parity"]).reshape(case.m, case.t)
+        ok = path.unrecovered[case.b:] == 0
+        assert np.array_equal(got[ok], par[ok])
+    return path
+
+
+@pytest.mark.parametrize("t", [1024, 16, 48, 4096 + 16])
+def test_config1_plain_lt(t):
+    """k=100 x t, RSD(0.1, 0.05), n=150, 30 erasures (usually a stall)."""
+    case = Case(100, 0, 150, t, gen.DIST_RSD, 0.1, 0.05)
+    _, _, cd = case.encode_gpu()
+    _, want = oracle.encode(case.g, case.data, t)
+    assert np.array_equal(_host(cd), want)
+    for s in range(3):
+        erased = np.zeros(150, np.uint8)
+        erased[gen.sample_indices(150, 30, gen.SEED_ERASE + (s << gen.ROUND_SHIFT))] = 1
+        _check_decode(case, want, cd, erased)
+    # nothing erased, then everything erased
+    _check_decode(case, want, cd, np.zeros(150, np.uint8))
+    _check_decode(case, want, cd, np.ones(150, np.uint8))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_precoded_midsize_both_modes(mode):
+    case = Case(700, 40, 950, 272, gen.DIST_FINITE40, mode=mode)
+    _, p, cd = case.encode_gpu()
+    par, cod = oracle.encode(case.g, case.data, case.t)
+    assert np.array_equal(_host(p), par) and np.array_equal(_host(cd), cod)
+    for s, frac in enumerate((0.1, 0.2, 0.3)):
+        _check_decode(case, cod, cd, _erased(case.n, frac, gen.SEED_ERASE + (s << 20)))
+
+
+def test_config2_full_size_encode_decode():
+    """k=4096 x 64 KiB, 128 checks (3 per data block), n=5400, FiniteDist
+    max-degree-40, 20% erasures: full comparison with the oracle."""
+    case = Case(4096, 128, 5400, 65536, gen.DIST_FINITE40)
+    _, p, cd = case.encode_gpu()
+    par, cod = oracle.encode(case.g, case.data, case.t)
+    assert np.array_equal(_host(p), par)
+    assert np.array_equal(_host(cd), cod)
+    path = _check_decode(case, cod, cd, _erased(case.n, 0.2, gen.SEED_ERASE))
+    assert path.unrecovered.sum() == 0
+    # a stalled draw is reproduced exactly too
+    _check_decode(case, cod, cd, _erased(case.n, 0.2, gen.SEED_ERASE + (2 << 20)))
+
+
+def test_update_and_repair_rounds():
+    """Config-4 shape at reduced t: rewrite 1% of data, then repair 5% of coded."""
+    import torch
+    b, m, n, t = 4096, 128, 5400, 4096
+    case = Case(b, m, n, t, gen.DIST_FINITE40)
+    d, p, cd = case.encode_gpu()
+    data = case.data.copy()
+    u = gen.round_count(0.01, b)
+    ws_u = case.code.workspace(_fs().OP_UPDATE, u)
+    ws_r = case.code.workspace(_fs().OP_REPAIR)
+    for rnd in range(2):
+        idx = gen.sample_indices(b, u, gen.SEED_UPDATE + (rnd << gen.ROUND_SHIFT))
+        new = gen.fill_bytes(gen.SEED_NEWDATA + (rnd << gen.ROUND_SHIFT), u * t).reshape(u, t)
+        case.code.update(_dev(idx), u, _dev(new), d, p, cd, ws_u)
+        data, par, cod = oracle.update(case.g, data, idx, new, t)
+        assert case.code.ws_status(ws_u) == 0
+        assert np.array_equal(_host(d), data)
+        assert np.array_equal(_host(p), par)
+        assert np.array_equal(_host(cd), cod)
+        nl = gen.round_count(0.05, n)
+        lost = gen.sample_indices(n, nl, gen.SEED_REPAIR + (rnd << gen.ROUND_SHIFT))
+        cd[torch.from_numpy(lost).long().cuda()] = 0
+        case.code.repair(_dev(lost), nl, d, p, cd, ws_r)
+        assert case.code.ws_status(ws_r) == 0
+        assert np.array_equal(_host(cd), cod)
+
+
+def test_encode_rows_and_empty_calls():
+    import torch
+    case = Case(300, 12, 420, 64, gen.DIST_FINITE40)
+    d, p, cd = case.encode_gpu()
+    _, cod = oracle.encode(case.g, case.data, case.t)
+    cd2 = torch.zeros_like(cd)
+    ws = case.code.workspace(_fs().OP_ENCODE)
+    case.code.encode_rows(100, 250, d, p, cd2, ws)
+    torch.cuda.synchronize()
+    got = _host(cd2)
+    assert np.array_equal(got[100:250], cod[100:250]) and not got[:100].any() and not got[250:].any()
+    # n_idx = 0 and n_lost = 0 leave everything untouched
+    before = (_host(d).copy(), _host(p).copy(), _host(cd).copy())
+    case.code.update(None, 0, None, d, p, cd, case.code.workspace(_fs().OP_UPDATE, 0))
+    case.code.repair(None, 0, d, p, cd, case.code.workspace(_fs().OP_REPAIR))
+    torch.cuda.synchronize()
+    assert all(np.array_equal(x, y) for x, y in zip(before, (_host(d), _host(p), _host(cd))))
+
+
+def test_device_detected_bad_indices():
+    import torch
+    fs = _fs()
+    case = Case(200, 8, 260, 32, gen.DIST_FINITE40)
+    d, p, cd = case.encode_gpu()
+    snapshot = (_host(d).copy(), _host(p).copy(), _host(cd).copy())
+    new = _dev(np.zeros((2, 32), np.uint8))
+    ws = case.code.workspace(fs.OP_UPDATE, 2)
+    case.code.update(_dev(np.array([5, 5], np.int32)), 2, new, d, p, cd, ws)   # repeated
+    assert case.code.ws_status(ws) == fs.FS_ERR_INVALID
+    case.code.update(_dev(np.array([5, 200], np.int32)), 2, new, d, p, cd, ws)  # out of range
+    assert case.code.ws_status(ws) == fs.FS_ERR_INVALID
+    # a rejected update changes nothing
+    assert all(np.array_equal(x, y) for x, y in zip(snapshot, (_host(d), _host(p), _host(cd))))
+    wr = case.code.workspace(fs.OP_REPAIR)
+    case.code.repair(_dev(np.array([3, 260, -1], np.int32)), 3, d, p, cd, wr)
+    assert case.code.ws_status(wr) == fs.FS_ERR_INVALID
+    _, cod = oracle.encode(case.g, case.data, 32)
+    assert np.array_equal(_host(cd), cod)  # row 3 recomputed to the same bytes
+    # a clean call on the same workspace reads FS_OK again
+    case.code.repair(_dev(np.array([3], np.int32)), 1, d, p, cd, wr)
+    assert case.code.ws_status(wr) == fs.FS_OK
+
+
+def test_host_side_rejections():
+    import torch
+    fs = _fs()
+    case = Case(64, 0, 90, 32, gen.DIST_RSD, 0.1, 0.05)
+    d = torch.zeros(64 * 32 + 16, dtype=torch.uint8, device="cuda")
+    cd = torch.zeros(90 * 32 + 16, dtype=torch.uint8, device="cuda")
+    ws = case.code.workspace(fs.OP_ENCODE)
+    with pytest.raises(fs.FounsureError) as ei:
+        case.code.encode(d[1:], None, cd, ws)      # misaligned input
+    assert ei.value.status == fs.FS_ERR_INVALID
+    with pytest.raises(fs.FounsureError):
+        case.code.encode(d, d, cd, ws)              # parity given for m == 0
+    g = case.g
+    bad = gen.Graph(g.b, 0, g.n, g.pre_ptr, g.pre_idx, g.lt_ptr, g.lt_idx.copy())
+    bad.lt_idx[0] = 10 ** 6
+    with pytest.raises(fs.FounsureError):
+        fs.Code(bad, 32)
+    with pytest.raises(fs.FounsureError):
+        fs.Code(g, 24)                               # t not a multiple of 16
+
+
+def test_zero_coded_rows():
+    import torch
+    fs = _fs()
+    g = gen.Graph(4, 0, 0, np.zeros(1, np.int32), np.zeros(0, np.int32),
+                  np.zeros(1, np.int32), np.zeros(0, np.int32))
+    code = fs.Code(g, 16)
+    out = torch.full((4, 16), 7, dtype=torch.uint8, device="cuda")
+    unrec = torch.empty(4, dtype=torch.uint8, device="cuda")
+    nun = torch.empty(1, dtype=torch.int32, device="cuda")
+    code.decode(None, None, out, unrec, nun, code.workspace(fs.OP_DECODE))
+    torch.cuda.synchronize()
+    assert not _host(out).any() and _host(unrec).all() and int(_host(nun)[0]) == 4
