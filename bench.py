@@ -1,0 +1,460 @@
+"""Throughput of the Founsure GF(2) gather-XOR path on one GB300 (or N replicas).
+
+One step is one pass of the whole hot path over one precoded stripe:
+  encode   - precode parities + LT/LDGM coded blocks (fs_encode)
+  decode   - Algorithm 5 schedule + its payload (fs_decode_schedule,
+             fs_decode_payload) of the coded blocks with 20% erased
+  update   - 1% of data blocks rewritten, deltas pushed into parities and
+             coded blocks (fs_update)
+  repair   - 5% of coded blocks recomputed from the intermediates (fs_repair)
+Workload: b=4096 data blocks x 64 KiB (256 MiB), 128 precode checks (each data
+block in 3), n=5400 coded blocks, max-degree-40 FiniteDist degrees, seeded
+synthetic bytes. Every input is larger than the 129 MB L2, so no flush is
+needed between steps.
+
+value = (data bytes encoded + data bytes recovered by decode) / step time,
+steps timed with CUDA events on the launching stream. Per-op times come from
+events around each call on the same stream.
+
+--impl reference times the CPU oracle (plain C loops, one core) on a byte
+slice of every block of the same stripe and prints the same JSON line.
+Under torchrun each rank runs its own stripe (replicas; no data exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1702_07409_gb300 import gen  # noqa: E402
+
+B, M, N_CODED, T = 4096, 128, 5400, 65536
+ERASE_FRAC, UPDATE_FRAC, REPAIR_FRAC = 0.20, 0.01, 0.05
+METRIC = "encode & BP-decode source GB/s"
+WORKLOAD = ("precoded LDGM stripe: b=4096 x 64 KiB data, m=128 checks (3 per data block), "
+            "n=5400, FiniteDist max-degree-40, 20% erasures; step = encode + decode + "
+            "1% update + 5% repair")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def reduce_max(x: float, device) -> float:
+    """Max of x over ranks (x itself on a single process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=reasons, samples=len(rows))
+        return out
+
+
+class Stripe:
+    """Device-resident state of one stripe and the seeded inputs of its steps."""
+
+    def __init__(self, stripe: int, n_rounds: int, device, tuning=None, overlap=True):
+        import torch
+        self.overlap = overlap
+        self.side = torch.cuda.Stream(device=device)
+        from paper_1702_07409_gb300 import founsure as fs
+        self.fs = fs
+        off = stripe << gen.STRIPE_SHIFT
+        self.g = gen.make_graph(B, M, N_CODED, gen.DIST_FINITE40, stripe=stripe)
+        self.code = fs.Code(self.g, T)
+        if tuning:
+            for knob, value in tuning.items():
+                self.code.set_tuning(knob, value)
+        host = gen.fill_bytes(gen.SEED_DATA + off, B * T).reshape(B, T)
+        self.host_data = torch.from_numpy(host).pin_memory()
+        self.d = self.host_data.to(device)
+        self.p = torch.empty((M, T), dtype=torch.uint8, device=device)
+        self.cd = torch.empty((N_CODED, T), dtype=torch.uint8, device=device)
+        self.out = torch.empty((B, T), dtype=torch.uint8, device=device)
+        self.unrec = torch.empty(B + M, dtype=torch.uint8, device=device)
+        self.nun = torch.empty(1, dtype=torch.int32, device=device)
+        er = np.zeros(N_CODED, np.uint8)
+        er[gen.sample_indices(N_CODED, gen.round_count(ERASE_FRAC, N_CODED),
+                              gen.SEED_ERASE + off)] = 1
+        self.host_erased = torch.from_numpy(er).pin_memory()
+        self.erased = self.host_erased.to(device)
+        self.u = gen.round_count(UPDATE_FRAC, B)
+        self.nl = gen.round_count(REPAIR_FRAC, N_CODED)
+        self.n_rounds = n_rounds
+        idx, new, lost = [], [], []
+        for r in range(n_rounds):
+            idx.append(gen.sample_indices(B, self.u, gen.SEED_UPDATE + off + (r << gen.ROUND_SHIFT)))
+            new.append(gen.fill_bytes(gen.SEED_NEWDATA + off + (r << gen.ROUND_SHIFT),
+                                      self.u * T).reshape(self.u, T))
+            lost.append(gen.sample_indices(N_CODED, self.nl,
+                                           gen.SEED_REPAIR + off + (r << gen.ROUND_SHIFT)))
+        self.host_idx = torch.from_numpy(np.stack(idx)).pin_memory()
+        self.host_new = torch.from_numpy(np.stack(new)).pin_memory()
+        self.host_lost = torch.from_numpy(np.stack(lost)).pin_memory()
+        self.idx = self.host_idx.to(device)
+        self.new = self.host_new.to(device)
+        self.lost = self.host_lost.to(device)
+        self.ws_e = self.code.workspace(fs.OP_ENCODE, device=device)
+        self.ws_d = self.code.workspace(fs.OP_DECODE, device=device)
+        self.ws_u = self.code.workspace(fs.OP_UPDATE, self.u, device=device)
+        self.ws_r = self.code.workspace(fs.OP_REPAIR, device=device)
+        self.host_out = torch.empty((B, T), dtype=torch.uint8).pin_memory()
+        self.host_nun = torch.empty(1, dtype=torch.int32).pin_memory()
+        self.nun_reads = []
+
+    # launches of this library's kernels per step (encode 2, decode 2,
+    # update 5, repair 1)
+    LAUNCHES_PER_STEP = 10
+
+    def step(self, r: int, ev=None):
+        """encode, decode (schedule + payload), update, repair. The decoding
+        schedule needs only the erasure flags, so with overlap on it runs on a
+        side stream beside the encode (the payload waits for both)."""
+        import torch
+        c = self.code
+        r %= self.n_rounds
+        main = torch.cuda.current_stream()
+        if self.overlap:
+            self.side.wait_stream(main)
+            with torch.cuda.stream(self.side):
+                if ev: ev[6].record()
+                c.decode_schedule(self.erased, self.unrec, self.nun, self.ws_d)
+                if ev: ev[7].record()
+        if ev: ev[0].record()
+        c.encode(self.d, self.p, self.cd, self.ws_e)
+        if ev: ev[1].record()
+        if self.overlap:
+            main.wait_stream(self.side)
+        else:
+            if ev: ev[6].record()
+            c.decode_schedule(self.erased, self.unrec, self.nun, self.ws_d)
+            if ev: ev[7].record()
+        if ev: ev[2].record()
+        c.decode_payload(self.cd, self.out, self.ws_d)
+        if ev: ev[3].record()
+        c.update(self.idx[r], self.u, self.new[r], self.d, self.p, self.cd, self.ws_u)
+        if ev: ev[4].record()
+        c.repair(self.lost[r], self.nl, self.d, self.p, self.cd, self.ws_r)
+        if ev: ev[5].record()
+
+    def step_e2e(self, r: int):
+        """The same step from pinned host buffers: inputs copied in, the
+        decoded data and the unrecovered count copied back."""
+        r %= self.n_rounds
+        self.d.copy_(self.host_data, non_blocking=True)
+        self.erased.copy_(self.host_erased, non_blocking=True)
+        self.idx[r].copy_(self.host_idx[r], non_blocking=True)
+        self.new[r].copy_(self.host_new[r], non_blocking=True)
+        self.lost[r].copy_(self.host_lost[r], non_blocking=True)
+        self.step(r)
+        self.host_out.copy_(self.out, non_blocking=True)
+        self.host_nun.copy_(self.nun, non_blocking=True)
+
+    def h2d_bytes(self):
+        return B * T + N_CODED + self.u * 4 + self.u * T + self.nl * 4
+
+    def d2h_bytes(self):
+        return B * T + 4
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+    peak, peak_kind = peaks()
+    from paper_1702_07409_gb300 import founsure as fs
+    tuning = {}
+    if args.peel_ctas:
+        tuning[fs.TUNE_PEEL_CTAS] = args.peel_ctas
+    if args.gather_ctas:
+        tuning[fs.TUNE_GATHER_CTAS] = args.gather_ctas
+    st = Stripe(rank, max(args.steps, 1) + args.warmup, device, tuning,
+                overlap=not args.serial_schedule)
+    torch.cuda.synchronize()
+
+    # warm-up; also checks the decode outcome of this erasure draw
+    for r in range(args.warmup):
+        st.step(r)
+    torch.cuda.synchronize()
+    n_unrec = int(st.nun.item())
+    unrec_data = int(st.unrec[:B].sum().item())
+    recovered = (B - unrec_data) * T
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(K)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0.record()
+        for i in range(K):
+            st.step(args.warmup + i, evs[i])
+        t1.record()
+        torch.cuda.synchronize()
+    barrier()
+    ms_total = reduce_max(t0.elapsed_time(t1), device)
+    ms_step = ms_total / K
+    spans = {"encode": (0, 1), "decode_schedule": (6, 7), "decode_payload": (2, 3),
+             "update": (3, 4), "repair": (4, 5)}
+    op_ms = {o: statistics.mean(evs[i][a].elapsed_time(evs[i][b]) for i in range(K))
+             for o, (a, b) in spans.items()}
+
+    # e2e: the same steps from pinned host memory, copies inside the timed region
+    for r in range(min(args.warmup, 2)):
+        st.step_e2e(r)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(K):
+        st.step_e2e(args.warmup + i)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = reduce_max(e0.elapsed_time(e1), device) / K
+
+    src_bytes = B * T + recovered
+    gbs = world * src_bytes / (ms_step * 1e-3) / 1e9
+    gbs_e2e = world * src_bytes / (ms_e2e * 1e-3) / 1e9
+
+    # roofline of the encode launches: algorithmic bytes = data read once,
+    # parities written, coded blocks written
+    enc_bytes = (B + M + N_CODED) * T
+    enc_gbs = enc_bytes / (op_ms["encode"] * 1e-3) / 1e9
+    g = st.g
+    dec_pairs_lt = None
+    try:
+        view = st.code.decode_path(st.ws_d)
+        pg = view["pair_g"].cpu().numpy()
+        dec_pairs_lt = int((pg < N_CODED).sum())
+    except Exception:
+        pass
+    dec_bytes = ((dec_pairs_lt or 0) + (B - unrec_data)) * T
+    dec_gbs = dec_bytes / (op_ms["decode_payload"] * 1e-3) / 1e9
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded splitmix64 bytes and graphs)",
+        "config": {"workload": WORKLOAD, "b": B, "m": M, "n": N_CODED, "block_bytes": T,
+                   "e_lt": g.e_lt, "e_pre": g.e_pre, "erased": int(st.erased.sum().item()),
+                   "unrecovered": n_unrec, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "schedule_beside_encode": not args.serial_schedule,
+                   "tuning": {"peel_ctas": args.peel_ctas or 1,
+                              "gather_ctas": args.gather_ctas or 8}},
+        "ops_ms": {k: round(v, 4) for k, v in op_ms.items()},
+        "encode_source_gbs": round(B * T / (op_ms["encode"] * 1e-3) / 1e9, 1),
+        "decode_source_gbs": round(recovered / ((op_ms["decode_schedule"] +
+                                                  op_ms["decode_payload"]) * 1e-3) / 1e9, 1),
+        "roofline": {"bound": "hbm", "kernel": "fs_encode (precode + LT gather launches)",
+                     "achieved": round(enc_gbs, 1), "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": round(enc_gbs / peak, 4), "traffic": None,
+                     "algorithmic_bytes": enc_bytes},
+        "decode_payload_roofline": {"achieved": round(dec_gbs, 1), "frac": round(dec_gbs / peak, 4),
+                                    "algorithmic_bytes": dec_bytes},
+        "e2e": {"value": round(gbs_e2e, 2), "unit": "GB/s", "ms_per_step": round(ms_e2e, 4),
+                "h2d_bytes_per_step": st.h2d_bytes(), "d2h_bytes_per_step": st.d2h_bytes()},
+        "gpu_launches": Stripe.LAUNCHES_PER_STEP * K,
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                   "reasons": clocks["reasons"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_slice)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def _oracle_step(g, data, erased, idx, new, lost, t):
+    import oracle
+    par, cod = oracle.encode(g, data, t)
+    out, path = oracle.decode(g, cod, erased, t)
+    data, par, cod = oracle.update(g, data, idx, new, t)
+    oracle.repair(g, data, lost, t)
+    return out, path, data
+
+
+def cpu_baseline(slice_bytes: int, steps: int = 2):
+    """The oracle timed on a byte slice of every block of the same stripe."""
+    import oracle
+    oracle.build()
+    g = gen.make_graph(B, M, N_CODED, gen.DIST_FINITE40)
+    t = slice_bytes
+    data = gen.fill_bytes(gen.SEED_DATA, B * t).reshape(B, t)
+    er = np.zeros(N_CODED, np.uint8)
+    er[gen.sample_indices(N_CODED, gen.round_count(ERASE_FRAC, N_CODED), gen.SEED_ERASE)] = 1
+    u, nl = gen.round_count(UPDATE_FRAC, B), gen.round_count(REPAIR_FRAC, N_CODED)
+    src = 0
+    t0 = time.perf_counter()
+    for r in range(steps):
+        idx = gen.sample_indices(B, u, gen.SEED_UPDATE + (r << gen.ROUND_SHIFT))
+        new = gen.fill_bytes(gen.SEED_NEWDATA + (r << gen.ROUND_SHIFT), u * t).reshape(u, t)
+        lost = gen.sample_indices(N_CODED, nl, gen.SEED_REPAIR + (r << gen.ROUND_SHIFT))
+        out, path, data = _oracle_step(g, data, er, idx, new, lost, t)
+        src += B * t + int((path.unrecovered[:B] == 0).sum()) * t
+    dt = time.perf_counter() - t0
+    return {"value": round(src / dt / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "%d steps of the same stripe, graph and erasures on a %d-byte slice of "
+                      "every block (full block 65536 B)" % (steps, t),
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    g = gen.make_graph(B, M, N_CODED, gen.DIST_FINITE40)
+    t = args.cpu_slice
+    data = gen.fill_bytes(gen.SEED_DATA, B * t).reshape(B, t)
+    er = np.zeros(N_CODED, np.uint8)
+    er[gen.sample_indices(N_CODED, gen.round_count(ERASE_FRAC, N_CODED), gen.SEED_ERASE)] = 1
+    u, nl = gen.round_count(UPDATE_FRAC, B), gen.round_count(REPAIR_FRAC, N_CODED)
+
+    def one(r, data):
+        idx = gen.sample_indices(B, u, gen.SEED_UPDATE + (r << gen.ROUND_SHIFT))
+        new = gen.fill_bytes(gen.SEED_NEWDATA + (r << gen.ROUND_SHIFT), u * t).reshape(u, t)
+        lost = gen.sample_indices(N_CODED, nl, gen.SEED_REPAIR + (r << gen.ROUND_SHIFT))
+        out, path, data = _oracle_step(g, data, er, idx, new, lost, t)
+        return data, B * t + int((path.unrecovered[:B] == 0).sum()) * t
+
+    for r in range(args.warmup):
+        data, _ = one(r, data)
+    src = 0
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        data, s = one(args.warmup + i, data)
+        src += s
+    dt = time.perf_counter() - t0
+    v = src / dt / 1e9
+    ms = dt * 1e3 / max(args.steps, 1)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded splitmix64 bytes and graphs)",
+        "config": {"workload": WORKLOAD, "b": B, "m": M, "n": N_CODED, "block_bytes": T,
+                   "sample_block_bytes": t},
+        "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "each step: the same stripe on a %d-byte slice of every "
+                                   "block" % t},
+        "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-slice", type=int, default=16384,
+                    help="bytes of each block the CPU oracle processes per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serial-schedule", action="store_true",
+                    help="run the decoding schedule after the encode instead of beside it")
+    ap.add_argument("--peel-ctas", type=int, default=0, help="tuning knob (1..8)")
+    ap.add_argument("--gather-ctas", type=int, default=0, help="tuning knob (1..16)")
+    ap.add_argument("--block-bytes", type=int, default=65536,
+                    help="block size t (default 65536; smaller only for profiling captures)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps
+    globals()["T"] = args.block_bytes
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -99,6 +99,18 @@ void fs_code_destroy(fs_code *code);
 fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
                        size_t *block_bytes);
 
+/* Tuning knobs of a code. They change speed only, never a result.
+ *   FS_TUNE_PEEL_CTAS    payload-peel CTAs per SM; each owns a slice of
+ *                        every block sized so all slices run at once
+ *                        (1..8; default 1)
+ *   FS_TUNE_GATHER_CTAS  resident CTAs per SM of the gather kernels
+ *                        (1..16; default 8)
+ * Returns FS_ERR_INVALID for an unknown knob or an out-of-range value. Not
+ * thread-safe against concurrent hot calls on the same code. */
+#define FS_TUNE_PEEL_CTAS   1
+#define FS_TUNE_GATHER_CTAS 2
+fs_status fs_code_set_tuning(fs_code *code, int knob, int value);
+
 /* Bytes of caller-provided device workspace that op needs. n_items is the
  * largest n_idx an FS_OP_UPDATE call will pass (ignored for other ops).
  * Workspaces are 256-byte aligned by the caller; one workspace must not be

@@ -9,7 +9,6 @@
 
 #include "fs_internal.cuh"
 
-size_t dpg_smem_bytes(const fs_code *c);
 
 namespace {
 
@@ -48,6 +47,7 @@ void free_code(fs_code *c) {
     if (!c) return;
     cudaFree(c->con_ptr);
     cudaFree(c->con_idx);
+    cudaFree(c->con_xs);
     cudaFree(c->pre_ptr);
     cudaFree(c->pre_idx);
     cudaFree(c->var_ptr);
@@ -103,8 +103,14 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
         con_idx[o++] = b + j;  // larger than every member: rows stay ascending
         con_ptr[n + j + 1] = (int32_t)o;
     }
-    for (int32_t g = 0; g < n_con; ++g)
+    // per constraint: degree bound and the XOR of its variable indices (the
+    // symbolic peel keeps this XOR over the still-unknown variables, so a
+    // constraint with one unknown names it without a scan)
+    std::vector<int32_t> con_xs((size_t)n_con, 0);
+    for (int32_t g = 0; g < n_con; ++g) {
         max_con_deg = std::max(max_con_deg, con_ptr[g + 1] - con_ptr[g]);
+        for (int32_t e = con_ptr[g]; e < con_ptr[g + 1]; ++e) con_xs[g] ^= con_idx[e];
+    }
     // transpose: constraints containing each intermediate, ascending
     std::vector<int32_t> var_ptr((size_t)k_int + 1, 0), var_idx((size_t)e_con);
     for (int64_t e = 0; e < e_con; ++e) var_ptr[con_idx[e] + 1]++;
@@ -137,6 +143,8 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     c->e_con = e_con;
     c->max_con_deg = max_con_deg;
     c->max_var_deg = max_var_deg;
+    c->peel_ctas = 1;
+    c->gather_ctas = 8;
     cudaError_t e = cudaGetDevice(&c->device);
     int v = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c->device);
@@ -146,6 +154,7 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     c->smem_optin = (size_t)(v > 1024 ? v - 1024 : 0);
     if (e == cudaSuccess) e = upload(&c->con_ptr, con_ptr);
     if (e == cudaSuccess) e = upload(&c->con_idx, con_idx);
+    if (e == cudaSuccess) e = upload(&c->con_xs, con_xs);
     if (e == cudaSuccess) e = upload(&c->pre_ptr, pre_ptr);
     if (e == cudaSuccess) e = upload(&c->pre_idx, pre_idx);
     if (e == cudaSuccess) e = upload(&c->var_ptr, var_ptr);
@@ -174,10 +183,25 @@ FS_API fs_status fs_code_info(const fs_code *c, int32_t *b, int32_t *m, int32_t 
     return FS_OK;
 }
 
+FS_API fs_status fs_code_set_tuning(fs_code *c, int knob, int value) {
+    if (!c) return FS_ERR_INVALID;
+    switch (knob) {
+        case FS_TUNE_PEEL_CTAS:
+            if (value < 1 || value > 8) return FS_ERR_INVALID;
+            c->peel_ctas = value;
+            return FS_OK;
+        case FS_TUNE_GATHER_CTAS:
+            if (value < 1 || value > 16) return FS_ERR_INVALID;
+            c->gather_ctas = value;
+            return FS_OK;
+    }
+    return FS_ERR_INVALID;
+}
+
 FS_API size_t fs_workspace_bytes(const fs_code *c, int op, int32_t n_items) {
     if (!c) return 0;
     switch (op) {
-        case FS_OP_ENCODE: return WS_HDR_BYTES;
+        case FS_OP_ENCODE: return encode_ws_bytes(c);
         case FS_OP_REPAIR: return WS_HDR_BYTES;
         case FS_OP_DECODE: return decode_layout(c).total;
         case FS_OP_UPDATE: return update_layout(c, n_items < 0 ? 0 : n_items).total;
@@ -213,26 +237,8 @@ FS_API fs_status fs_encode(const fs_code *c, const void *d_data, void *d_parity,
     if ((c->m > 0) != (d_parity != nullptr)) return FS_ERR_INVALID;
     if (!aligned16(d_data) || !aligned16(d_parity) || !aligned16(d_coded) || !aligned16(d_ws))
         return FS_ERR_INVALID;
-    cudaStream_t s = as_stream(stream);
-    cudaError_t e = cudaSuccess;
-    if (c->m > 0) {
-        GatherArgs a;
-        a.ptr = c->pre_ptr;
-        a.idx = c->pre_idx;
-        a.rows = nullptr;
-        a.n_rows = c->m;
-        a.row_base = 0;
-        a.n_valid = c->m;
-        a.inA = static_cast<const uint4 *>(d_data);
-        a.inB = nullptr;
-        a.split = c->b;
-        a.out = static_cast<uint4 *>(d_parity);
-        a.tw = c->tw;
-        a.status = static_cast<int32_t *>(d_ws) + WS_STATUS;
-        e = launch_gather(a, c->num_sms, s);
-    }
-    if (e == cudaSuccess) e = launch_gather(lt_args(c, d_data, d_parity, d_coded, d_ws), c->num_sms, s);
-    return cuda_status(e);
+    return cuda_status(launch_encode(c, d_data, d_parity, d_coded, static_cast<uint8_t *>(d_ws),
+                                     as_stream(stream)));
 }
 
 FS_API fs_status fs_encode_rows(const fs_code *c, int32_t row_begin, int32_t row_end,
@@ -248,7 +254,7 @@ FS_API fs_status fs_encode_rows(const fs_code *c, int32_t row_begin, int32_t row
     GatherArgs a = lt_args(c, d_data, d_parity, d_coded, d_ws);
     a.row_base = row_begin;
     a.n_rows = row_end - row_begin;
-    if (e == cudaSuccess) e = launch_gather(a, c->num_sms, s);
+    if (e == cudaSuccess) e = launch_gather(a, c->num_sms, c->gather_ctas, s);
     return cuda_status(e);
 }
 
@@ -325,6 +331,6 @@ FS_API fs_status fs_repair(const fs_code *c, const int32_t *d_lost, int32_t n_lo
     GatherArgs a = lt_args(c, d_data, d_parity, d_coded, d_ws);
     a.rows = d_lost;
     a.n_rows = n_lost;
-    if (e == cudaSuccess) e = launch_gather(a, c->num_sms, s);
+    if (e == cudaSuccess) e = launch_gather(a, c->num_sms, c->gather_ctas, s);
     return cuda_status(e);
 }

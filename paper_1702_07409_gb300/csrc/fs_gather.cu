@@ -71,20 +71,30 @@ struct UpdArgs {
     const uint4 *d_new;
     uint4 *data, *parity, *coded;
     uint4 *delta, *pdelta;
-    int32_t *mark, *pmark;
-    const int32_t *con_ptr, *con_idx, *pre_ptr, *pre_idx;
+    int32_t *mark, *pmark, *cmark, *plist, *clist;
+    int32_t *n_plist, *n_clist;
+    const int32_t *con_ptr, *con_idx, *pre_ptr, *pre_idx, *var_ptr, *var_idx;
     int32_t b, m, n;
     int64_t tw;
     int32_t *status;
 };
 
-// mark[i] = -1 for all data, pmark[j] = 0, status = FS_OK
+__device__ __forceinline__ bool upd_ok(const UpdArgs &a) {
+    return *(volatile int32_t *)a.status == FS_OK;
+}
+
+// mark[i] = -1, pmark[j] = cmark[g] = 0, list counts 0, status FS_OK
 __global__ void k_update_init(UpdArgs a) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i0 == 0) *a.status = FS_OK;
+    if (i0 == 0) {
+        *a.status = FS_OK;
+        *a.n_plist = 0;
+        *a.n_clist = 0;
+    }
     for (int64_t i = i0; i < a.b; i += stride) a.mark[i] = -1;
     for (int64_t j = i0; j < a.m; j += stride) a.pmark[j] = 0;
+    for (int64_t g = i0; g < a.n; g += stride) a.cmark[g] = 0;
 }
 
 // mark[idx[q]] = q; a repeated or out-of-range index flags the call invalid
@@ -100,35 +110,56 @@ __global__ void k_update_mark(UpdArgs a) {
     }
 }
 
-// delta_q = old XOR new; data block idx[q] <- new
-__global__ void __launch_bounds__(kGatherThreads) k_update_delta(UpdArgs a) {
-    if (*(volatile int32_t *)a.status != FS_OK) return;
-    const int64_t n_words = (int64_t)a.n_idx * a.tw;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_words; x += stride) {
-        const int64_t q = x / a.tw, w = x - q * a.tw;
-        const int32_t i = a.idx[q];
-        const uint4 nw = __ldg(a.d_new + x);
-        uint4 d = a.data[(int64_t)i * a.tw + w];
-        xor4(d, nw);
-        a.delta[x] = d;
-        a.data[(int64_t)i * a.tw + w] = nw;
+// Appends constraint c (containing a changed variable) to its list once.
+__device__ __forceinline__ void touch(const UpdArgs &a, int32_t c, bool coded_only) {
+    if (c < a.n) {
+        if (atomicExch(a.cmark + c, 1) == 0) a.clist[atomicAdd(a.n_clist, 1)] = c;
+    } else if (!coded_only) {
+        const int32_t j = c - a.n;
+        if (atomicExch(a.pmark + j, 1) == 0) a.plist[atomicAdd(a.n_plist, 1)] = j;
     }
 }
 
-// parity j ^= XOR of the deltas of its changed members; pdelta_j keeps that XOR
+// CTA q: delta_q = old ^ new, data block idx[q] <- new, and every constraint
+// containing that block (coded rows and checks) is listed.
+__global__ void __launch_bounds__(kGatherThreads) k_update_delta(UpdArgs a) {
+    if (!upd_ok(a)) return;
+    for (int32_t q = blockIdx.x; q < a.n_idx; q += gridDim.x) {
+        const int32_t i = a.idx[q];
+        for (int64_t w = threadIdx.x; w < a.tw; w += blockDim.x) {
+            const uint4 nw = __ldg(a.d_new + (int64_t)q * a.tw + w);
+            uint4 d = a.data[(int64_t)i * a.tw + w];
+            xor4(d, nw);
+            a.delta[(int64_t)q * a.tw + w] = d;
+            a.data[(int64_t)i * a.tw + w] = nw;
+        }
+        for (int32_t e = a.var_ptr[i] + threadIdx.x; e < a.var_ptr[i + 1]; e += blockDim.x)
+            touch(a, a.var_idx[e], false);
+    }
+}
+
+// CTA per changed check j: the coded rows containing parity b + j are listed.
+__global__ void k_update_plist(UpdArgs a) {
+    if (!upd_ok(a)) return;
+    const int32_t np = *(volatile int32_t *)a.n_plist;
+    for (int32_t k = blockIdx.x; k < np; k += gridDim.x) {
+        const int32_t v = a.b + a.plist[k];
+        for (int32_t e = a.var_ptr[v] + threadIdx.x; e < a.var_ptr[v + 1]; e += blockDim.x)
+            touch(a, a.var_idx[e], true);
+    }
+}
+
+// changed parity j ^= XOR of the deltas of its changed members; pdelta_j
+// keeps that XOR. Tiles (listed check, chunk), chunk-major.
 __global__ void __launch_bounds__(kGatherThreads)
 k_update_parity(UpdArgs a, int32_t chunk_w, int32_t n_chunks) {
-    if (*(volatile int32_t *)a.status != FS_OK) return;
-    const int64_t n_tiles = (int64_t)n_chunks * a.m;
+    if (!upd_ok(a)) return;
+    const int32_t np = *(volatile int32_t *)a.n_plist;
+    const int64_t n_tiles = (int64_t)n_chunks * np;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int32_t chunk = (int32_t)(tile / a.m);
-        const int32_t j = (int32_t)(tile - (int64_t)chunk * a.m);
+        const int32_t chunk = (int32_t)(tile / np);
+        const int32_t j = a.plist[tile - (int64_t)chunk * np];
         const int32_t e0 = a.pre_ptr[j], e1 = a.pre_ptr[j + 1];
-        bool any = false;
-        for (int32_t e = e0; e < e1 && !any; ++e) any = a.mark[a.pre_idx[e]] >= 0;
-        if (!any) continue;  // uniform over the CTA
-        if (chunk == 0 && threadIdx.x == 0) a.pmark[j] = 1;
         const int64_t w0 = (int64_t)chunk * chunk_w, w1 = min(w0 + chunk_w, a.tw);
         for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
             uint4 acc = make_uint4(0, 0, 0, 0);
@@ -144,21 +175,17 @@ k_update_parity(UpdArgs a, int32_t chunk_w, int32_t n_chunks) {
     }
 }
 
-// coded g ^= XOR of the deltas of its changed neighbours (data and parities)
+// listed coded row g ^= XOR of the deltas of its changed neighbours (data
+// blocks and parities). Tiles (listed row, chunk), chunk-major.
 __global__ void __launch_bounds__(kGatherThreads)
 k_update_coded(UpdArgs a, int32_t chunk_w, int32_t n_chunks) {
-    if (*(volatile int32_t *)a.status != FS_OK) return;
-    const int64_t n_tiles = (int64_t)n_chunks * a.n;
+    if (!upd_ok(a)) return;
+    const int32_t nc = *(volatile int32_t *)a.n_clist;
+    const int64_t n_tiles = (int64_t)n_chunks * nc;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int32_t chunk = (int32_t)(tile / a.n);
-        const int32_t g = (int32_t)(tile - (int64_t)chunk * a.n);
+        const int32_t chunk = (int32_t)(tile / nc);
+        const int32_t g = a.clist[tile - (int64_t)chunk * nc];
         const int32_t e0 = a.con_ptr[g], e1 = a.con_ptr[g + 1];
-        bool any = false;
-        for (int32_t e = e0; e < e1 && !any; ++e) {
-            const int32_t v = a.con_idx[e];
-            any = (v < a.b) ? (a.mark[v] >= 0) : (a.pmark[v - a.b] != 0);
-        }
-        if (!any) continue;
         const int64_t w0 = (int64_t)chunk * chunk_w, w1 = min(w0 + chunk_w, a.tw);
         for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
             uint4 acc = make_uint4(0, 0, 0, 0);
@@ -186,20 +213,20 @@ inline void chunking(int64_t tw, int32_t *chunk_w, int32_t *n_chunks, int *threa
     *threads = th < 32 ? 32 : th;
 }
 
-inline int grid_for(int64_t n_tiles, int num_sms) {
-    const int64_t cap = (int64_t)num_sms * kCtasPerSm;
+inline int grid_for(int64_t n_tiles, int num_sms, int ctas_per_sm = kCtasPerSm) {
+    const int64_t cap = (int64_t)num_sms * ctas_per_sm;
     const int64_t g = n_tiles < cap ? n_tiles : cap;
     return (int)(g < 1 ? 1 : g);
 }
 
 }  // namespace
 
-cudaError_t launch_gather(const GatherArgs &a, int num_sms, cudaStream_t s) {
+cudaError_t launch_gather(const GatherArgs &a, int num_sms, int ctas_per_sm, cudaStream_t s) {
     if (a.n_rows <= 0 || a.tw <= 0) return cudaSuccess;
     int32_t chunk_w, n_chunks;
     int threads;
     chunking(a.tw, &chunk_w, &n_chunks, &threads);
-    k_gather_xor<<<grid_for((int64_t)n_chunks * a.n_rows, num_sms), threads, 0, s>>>(a, chunk_w,
+    k_gather_xor<<<grid_for((int64_t)n_chunks * a.n_rows, num_sms, ctas_per_sm), threads, 0, s>>>(a, chunk_w,
                                                                                    n_chunks);
     return cudaGetLastError();
 }
@@ -218,29 +245,37 @@ cudaError_t launch_update(const fs_code *c, const int32_t *idx, int32_t n_idx, c
     a.pdelta = reinterpret_cast<uint4 *>(ws + L.pdelta);
     a.mark = reinterpret_cast<int32_t *>(ws + L.mark);
     a.pmark = reinterpret_cast<int32_t *>(ws + L.pmark);
+    a.cmark = reinterpret_cast<int32_t *>(ws + L.cmark);
+    a.plist = reinterpret_cast<int32_t *>(ws + L.plist);
+    a.clist = reinterpret_cast<int32_t *>(ws + L.clist);
+    a.n_plist = reinterpret_cast<int32_t *>(ws) + WS_COUNT_A;
+    a.n_clist = reinterpret_cast<int32_t *>(ws) + WS_COUNT_B;
     a.con_ptr = c->con_ptr;
     a.con_idx = c->con_idx;
     a.pre_ptr = c->pre_ptr;
     a.pre_idx = c->pre_idx;
+    a.var_ptr = c->var_ptr;
+    a.var_idx = c->var_idx;
     a.b = c->b;
     a.m = c->m;
     a.n = c->n;
     a.tw = c->tw;
     a.status = reinterpret_cast<int32_t *>(ws) + WS_STATUS;
 
-    const int64_t nb = c->b > c->m ? c->b : c->m;
+    int64_t nb = c->b > c->m ? c->b : c->m;
+    nb = nb > c->n ? nb : c->n;
     k_update_init<<<grid_for((nb + 255) / 256, c->num_sms), 256, 0, s>>>(a);
     if (n_idx > 0) {
         k_update_mark<<<grid_for((n_idx + 255) / 256, c->num_sms), 256, 0, s>>>(a);
-        const int64_t words = (int64_t)n_idx * c->tw;
-        k_update_delta<<<grid_for((words + kGatherThreads - 1) / kGatherThreads, c->num_sms),
-                         kGatherThreads, 0, s>>>(a);
+        k_update_delta<<<grid_for(n_idx, c->num_sms), kGatherThreads, 0, s>>>(a);
         int32_t chunk_w, n_chunks;
         int threads;
         chunking(c->tw, &chunk_w, &n_chunks, &threads);
-        if (c->m > 0)
+        if (c->m > 0) {
+            k_update_plist<<<grid_for(c->m, c->num_sms), 128, 0, s>>>(a);
             k_update_parity<<<grid_for((int64_t)n_chunks * c->m, c->num_sms), threads, 0, s>>>(
                 a, chunk_w, n_chunks);
+        }
         if (c->n > 0)
             k_update_coded<<<grid_for((int64_t)n_chunks * c->n, c->num_sms), threads, 0, s>>>(
                 a, chunk_w, n_chunks);

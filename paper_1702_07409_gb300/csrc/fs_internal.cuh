@@ -24,6 +24,7 @@ struct fs_code {
     // device arrays
     int32_t *con_ptr;     // [n_con + 1]
     int32_t *con_idx;     // [e_con]
+    int32_t *con_xs;      // [n_con] XOR of the variable indices of each constraint
     int32_t *pre_ptr;     // [m + 1]   precode rows (members only)
     int32_t *pre_idx;     // [e_pre]
     int32_t *var_ptr;     // [k_int + 1] transpose of the joint graph
@@ -31,7 +32,12 @@ struct fs_code {
     int device;
     int num_sms;
     size_t smem_optin;    // max dynamic shared memory per block
+    // tuning knobs (fs_code_set_tuning); they never change results
+    int peel_ctas;        // payload-peel CTAs per SM (slice width follows)
+    int gather_ctas;      // resident CTAs per SM for the gather kernels
 };
+
+constexpr int kRecipeSeg = 8;  // recipe entries one payload thread gathers at once
 
 // ---- workspace layouts (byte offsets from d_ws, 256-aligned) --------------
 static inline size_t fs_align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -45,12 +51,24 @@ enum {
     WS_COUNT_A = 4,     // scratch counters
     WS_COUNT_B = 5,
     WS_TILE_CTR = 6,
+    WS_STAGED = 7,      // 1: every level fits the payload kernel's shared-memory stages
     WS_HDR_BYTES = 256
 };
 
+// Decode workspace. The DPG state arrays (res .. lvl_o) are a spill area used
+// only when they do not fit in shared memory. The decoding path is written as
+// level_off[l] (first pair of level l), level_r0[l] (first recipe entry of
+// level l), level_s0[l] (first gather segment of level l), and per pair p:
+// pair_f, pair_g, recipe_off (first entry of its recipe), seg_off (first of
+// its gather segments), acc_slot (for a pair with several segments, its rank
+// among such pairs of its level, else -1); per segment: seg_pair (its pair,
+// counted from the first pair of the level). The recipe of pair p lists every
+// variable of constraint pair_g[p] (pair_f[p] included; the payload kernel
+// skips it); it is gathered in segments of at most kRecipeSeg entries.
 struct DecodeLayout {
-    size_t res, best, known, front_a, front_b, touched, pair_f, pair_g, level_off,
-        recipe_off, recipe_h, unrec_list, parity, total;
+    size_t res, xs, best, known, front_a, front_b, touched, lvl_o, lvl_v, pair_f, pair_g,
+        level_off, level_r0, level_s0, recipe_off, seg_off, acc_slot, seg_pair, recipe_h,
+        unrec_list, parity, total;
 };
 
 static inline DecodeLayout decode_layout(const fs_code *c) {
@@ -58,15 +76,23 @@ static inline DecodeLayout decode_layout(const fs_code *c) {
     size_t o = WS_HDR_BYTES;
     size_t K = (size_t)c->k_int, G = (size_t)c->n_con;
     L.res = o;        o = fs_align256(o + 4 * (G + 1));
+    L.xs = o;         o = fs_align256(o + 4 * (G + 1));
     L.best = o;       o = fs_align256(o + 8 * (K + 1));
     L.known = o;      o = fs_align256(o + (K + 1));
     L.front_a = o;    o = fs_align256(o + 4 * (G + 1));
     L.front_b = o;    o = fs_align256(o + 4 * (G + 1));
     L.touched = o;    o = fs_align256(o + 4 * (K + 1));
+    L.lvl_o = o;      o = fs_align256(o + 4 * (K + 1));
+    L.lvl_v = o;      o = fs_align256(o + 4 * (K + 1));
     L.pair_f = o;     o = fs_align256(o + 4 * (K + 1));
     L.pair_g = o;     o = fs_align256(o + 4 * (K + 1));
     L.level_off = o;  o = fs_align256(o + 4 * (K + 2));
+    L.level_r0 = o;   o = fs_align256(o + 4 * (K + 2));
+    L.level_s0 = o;   o = fs_align256(o + 4 * (K + 2));
     L.recipe_off = o; o = fs_align256(o + 4 * (K + 1));
+    L.seg_off = o;    o = fs_align256(o + 4 * (K + 1));
+    L.acc_slot = o;   o = fs_align256(o + 4 * (K + 1));
+    L.seg_pair = o;   o = fs_align256(o + 4 * (K + (size_t)c->e_con / kRecipeSeg + 2));
     L.recipe_h = o;   o = fs_align256(o + 4 * ((size_t)c->e_con + 1));
     L.unrec_list = o; o = fs_align256(o + 4 * (K + 1));
     L.parity = o;     o = fs_align256(o + (size_t)c->m * (size_t)c->t);
@@ -74,8 +100,12 @@ static inline DecodeLayout decode_layout(const fs_code *c) {
     return L;
 }
 
+// Update workspace: mark[i] = position of data block i in the index list or
+// -1; pmark[j] / cmark[g] flag changed checks / touched coded rows, listed in
+// plist / clist (counts in header words WS_COUNT_A / WS_COUNT_B); delta holds
+// old ^ new per listed block, pdelta the change of each changed parity.
 struct UpdateLayout {
-    size_t mark, pmark, delta, pdelta, total;
+    size_t mark, pmark, cmark, plist, clist, delta, pdelta, total;
 };
 
 static inline UpdateLayout update_layout(const fs_code *c, int32_t n_items) {
@@ -83,6 +113,9 @@ static inline UpdateLayout update_layout(const fs_code *c, int32_t n_items) {
     size_t o = WS_HDR_BYTES;
     L.mark = o;   o = fs_align256(o + 4 * ((size_t)c->b + 1));
     L.pmark = o;  o = fs_align256(o + 4 * ((size_t)c->m + 1));
+    L.cmark = o;  o = fs_align256(o + 4 * ((size_t)c->n + 1));
+    L.plist = o;  o = fs_align256(o + 4 * ((size_t)c->m + 1));
+    L.clist = o;  o = fs_align256(o + 4 * ((size_t)c->n + 1));
     L.delta = o;  o = fs_align256(o + (size_t)(n_items > 0 ? n_items : 0) * (size_t)c->t);
     L.pdelta = o; o = fs_align256(o + (size_t)c->m * (size_t)c->t);
     L.total = o;
@@ -108,7 +141,13 @@ struct GatherArgs {
     int64_t tw;
     int32_t *status;
 };
-cudaError_t launch_gather(const GatherArgs &a, int num_sms, cudaStream_t s);
+cudaError_t launch_gather(const GatherArgs &a, int num_sms, int ctas_per_sm, cudaStream_t s);
+
+// Encode (precode + LT) in one persistent launch; its workspace holds the
+// status word, a tile counter and one counter per byte chunk.
+size_t encode_ws_bytes(const fs_code *c);
+cudaError_t launch_encode(const fs_code *c, const void *data, void *parity, void *coded, uint8_t *ws,
+                          cudaStream_t s);
 
 // Decoding path generation (Algorithm 5), one CTA.
 cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws,

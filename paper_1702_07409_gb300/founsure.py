@@ -18,10 +18,12 @@ from . import _build
 FS_OK, FS_STALL, FS_ERR_INVALID, FS_ERR_CUDA, FS_ERR_NOMEM, FS_ERR_TIMEOUT = range(6)
 DECODE_JOINT, DECODE_TWO_PASS = 0, 1
 OP_ENCODE, OP_DECODE, OP_UPDATE, OP_REPAIR = 0, 1, 2, 3
+TUNE_PEEL_CTAS, TUNE_GATHER_CTAS = 1, 2
 WS_STATUS_OFFSET = 0
 
 #: every symbol declared in include/founsure_gpu.h
-EXPORTS = ("fs_code_create", "fs_code_destroy", "fs_code_info", "fs_workspace_bytes",
+EXPORTS = ("fs_code_create", "fs_code_destroy", "fs_code_info", "fs_code_set_tuning",
+           "fs_workspace_bytes",
            "fs_encode", "fs_encode_rows", "fs_decode", "fs_decode_schedule",
            "fs_decode_payload", "fs_decode_path", "fs_update", "fs_repair", "fs_status_string")
 
@@ -58,6 +60,8 @@ def lib() -> ctypes.CDLL:
         L.fs_code_destroy.restype = None
         L.fs_code_info.argtypes = [vp, vp, vp, vp, vp]
         L.fs_code_info.restype = ctypes.c_int
+        L.fs_code_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        L.fs_code_set_tuning.restype = ctypes.c_int
         L.fs_workspace_bytes.argtypes = [vp, ctypes.c_int, i32]
         L.fs_workspace_bytes.restype = sz
         L.fs_encode.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -159,6 +163,10 @@ class Code:
             self.close()
         except Exception:
             pass
+
+    def set_tuning(self, knob: int, value: int) -> None:
+        """Performance knob (fs_code_set_tuning); results never change."""
+        _check(lib().fs_code_set_tuning(self._h, knob, value), "fs_code_set_tuning")
 
     # -- workspaces -----------------------------------------------------------
     def workspace_bytes(self, op: int, n_items: int = 0) -> int:
