@@ -120,21 +120,28 @@ __device__ __forceinline__ void touch(const UpdArgs &a, int32_t c, bool coded_on
     }
 }
 
-// CTA q: delta_q = old ^ new, data block idx[q] <- new, and every constraint
-// containing that block (coded rows and checks) is listed.
-__global__ void __launch_bounds__(kGatherThreads) k_update_delta(UpdArgs a) {
+// Tiles (q, chunk): delta_q = old ^ new and data block idx[q] <- new over
+// the chunk; the chunk-0 tile of q also lists every constraint containing
+// that block (coded rows and checks).
+__global__ void __launch_bounds__(kGatherThreads)
+k_update_delta(UpdArgs a, int32_t chunk_w, int32_t n_chunks) {
     if (!upd_ok(a)) return;
-    for (int32_t q = blockIdx.x; q < a.n_idx; q += gridDim.x) {
+    const int64_t n_tiles = (int64_t)a.n_idx * n_chunks;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int32_t q = (int32_t)(tile / n_chunks);
+        const int32_t chunk = (int32_t)(tile - (int64_t)q * n_chunks);
         const int32_t i = a.idx[q];
-        for (int64_t w = threadIdx.x; w < a.tw; w += blockDim.x) {
+        const int64_t w0 = (int64_t)chunk * chunk_w, w1 = min(w0 + chunk_w, a.tw);
+        for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
             const uint4 nw = __ldg(a.d_new + (int64_t)q * a.tw + w);
             uint4 d = a.data[(int64_t)i * a.tw + w];
             xor4(d, nw);
             a.delta[(int64_t)q * a.tw + w] = d;
             a.data[(int64_t)i * a.tw + w] = nw;
         }
-        for (int32_t e = a.var_ptr[i] + threadIdx.x; e < a.var_ptr[i + 1]; e += blockDim.x)
-            touch(a, a.var_idx[e], false);
+        if (chunk == 0)
+            for (int32_t e = a.var_ptr[i] + threadIdx.x; e < a.var_ptr[i + 1]; e += blockDim.x)
+                touch(a, a.var_idx[e], false);
     }
 }
 
@@ -150,10 +157,15 @@ __global__ void k_update_plist(UpdArgs a) {
 }
 
 // changed parity j ^= XOR of the deltas of its changed members; pdelta_j
-// keeps that XOR. Tiles (listed check, chunk), chunk-major.
+// keeps that XOR. Tiles (listed check, chunk), chunk-major. Warp 0 first
+// lists the changed members of the check (32 members per step, ballot).
 __global__ void __launch_bounds__(kGatherThreads)
 k_update_parity(UpdArgs a, int32_t chunk_w, int32_t n_chunks) {
-    if (!upd_ok(a)) return;
+    __shared__ int32_t s_q[kGatherThreads];
+    __shared__ int s_nq, s_ok;
+    if (threadIdx.x == 0) s_ok = upd_ok(a);  // one decision for the whole CTA
+    __syncthreads();
+    if (!s_ok) return;
     const int32_t np = *(volatile int32_t *)a.n_plist;
     const int64_t n_tiles = (int64_t)n_chunks * np;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -161,17 +173,36 @@ k_update_parity(UpdArgs a, int32_t chunk_w, int32_t n_chunks) {
         const int32_t j = a.plist[tile - (int64_t)chunk * np];
         const int32_t e0 = a.pre_ptr[j], e1 = a.pre_ptr[j + 1];
         const int64_t w0 = (int64_t)chunk * chunk_w, w1 = min(w0 + chunk_w, a.tw);
+        if (threadIdx.x < 32) {
+            int nq = 0;
+            for (int32_t base = e0; base < e1; base += 32) {
+                const int32_t e = base + (int32_t)threadIdx.x;
+                const int32_t q = e < e1 ? a.mark[a.pre_idx[e]] : -1;
+                const unsigned hit = __ballot_sync(0xffffffffu, q >= 0);
+                const int pos = nq + __popc(hit & ((1u << threadIdx.x) - 1u));
+                if (q >= 0 && pos < kGatherThreads) s_q[pos] = q;
+                nq += __popc(hit);
+            }
+            if (threadIdx.x == 0) s_nq = nq;
+        }
+        __syncthreads();
+        const int nq = s_nq;
         for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
             uint4 acc = make_uint4(0, 0, 0, 0);
-            for (int32_t e = e0; e < e1; ++e) {
-                const int32_t q = a.mark[a.pre_idx[e]];
-                if (q >= 0) xor4(acc, a.delta[(int64_t)q * a.tw + w]);
+            if (nq <= kGatherThreads) {
+                for (int k = 0; k < nq; ++k) xor4(acc, a.delta[(int64_t)s_q[k] * a.tw + w]);
+            } else {  // more changed members than the list holds: scan the check
+                for (int32_t e = e0; e < e1; ++e) {
+                    const int32_t q = a.mark[a.pre_idx[e]];
+                    if (q >= 0) xor4(acc, a.delta[(int64_t)q * a.tw + w]);
+                }
             }
             a.pdelta[(int64_t)j * a.tw + w] = acc;
             uint4 p = a.parity[(int64_t)j * a.tw + w];
             xor4(p, acc);
             a.parity[(int64_t)j * a.tw + w] = p;
         }
+        __syncthreads();
     }
 }
 
@@ -267,10 +298,11 @@ cudaError_t launch_update(const fs_code *c, const int32_t *idx, int32_t n_idx, c
     k_update_init<<<grid_for((nb + 255) / 256, c->num_sms), 256, 0, s>>>(a);
     if (n_idx > 0) {
         k_update_mark<<<grid_for((n_idx + 255) / 256, c->num_sms), 256, 0, s>>>(a);
-        k_update_delta<<<grid_for(n_idx, c->num_sms), kGatherThreads, 0, s>>>(a);
         int32_t chunk_w, n_chunks;
         int threads;
         chunking(c->tw, &chunk_w, &n_chunks, &threads);
+        k_update_delta<<<grid_for((int64_t)n_idx * n_chunks, c->num_sms), kGatherThreads, 0, s>>>(
+            a, chunk_w, n_chunks);
         if (c->m > 0) {
             k_update_plist<<<grid_for(c->m, c->num_sms), 128, 0, s>>>(a);
             k_update_parity<<<grid_for((int64_t)n_chunks * c->m, c->num_sms), threads, 0, s>>>(

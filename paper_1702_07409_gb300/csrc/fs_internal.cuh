@@ -29,12 +29,17 @@ struct fs_code {
     int32_t *pre_idx;     // [e_pre]
     int32_t *var_ptr;     // [k_int + 1] transpose of the joint graph
     int32_t *var_idx;     // [e_con]
+    int32_t *chk_ptr;     // [k_int + 1] checks containing each intermediate
+    int32_t *chk_idx;     // [e_pre + m]  (data: its precode checks; parity b+j: j)
     int device;
     int num_sms;
     size_t smem_optin;    // max dynamic shared memory per block
     // tuning knobs (fs_code_set_tuning); they never change results
     int peel_ctas;        // payload-peel CTAs per SM (slice width follows)
     int gather_ctas;      // resident CTAs per SM for the gather kernels
+    int peel_chk_acc;     // 1: checks decode from shared-memory accumulators
+    int dpg_compact;      // 1: symbolic peel in the compact shared-memory form when it fits
+    int peel_prefetch;    // 1: the payload peel prefetches gathered blocks into L2
 };
 
 constexpr int kRecipeSeg = 8;  // recipe entries one payload thread gathers at once
@@ -55,20 +60,20 @@ enum {
     WS_HDR_BYTES = 256
 };
 
-// Decode workspace. The DPG state arrays (res .. lvl_o) are a spill area used
+// Decode workspace. The DPG state arrays (res .. known) are a spill area used
 // only when they do not fit in shared memory. The decoding path is written as
 // level_off[l] (first pair of level l), level_r0[l] (first recipe entry of
 // level l), level_s0[l] (first gather segment of level l), and per pair p:
-// pair_f, pair_g, recipe_off (first entry of its recipe), seg_off (first of
-// its gather segments), acc_slot (for a pair with several segments, its rank
+// pair_f, pair_g, pair_e0 (first entry of the row of pair_g in the joint
+// graph), recipe_off (first entry of its recipe), seg_off (first of its
+// gather segments), acc_slot (for a pair with several segments, its rank
 // among such pairs of its level, else -1); per segment: seg_pair (its pair,
-// counted from the first pair of the level). The recipe of pair p lists every
-// variable of constraint pair_g[p] (pair_f[p] included; the payload kernel
-// skips it); it is gathered in segments of at most kRecipeSeg entries.
+// counted from the first pair of the level). The recipe of pair p is the row
+// of constraint pair_g[p] (pair_f[p] included; the payload kernel skips it);
+// it is gathered in segments of at most kRecipeSeg entries.
 struct DecodeLayout {
-    size_t res, xs, best, known, front_a, front_b, touched, lvl_o, lvl_v, pair_f, pair_g,
-        level_off, level_r0, level_s0, recipe_off, seg_off, acc_slot, seg_pair, recipe_h,
-        unrec_list, parity, total;
+    size_t res, xs, best, known, front_a, front_b, touched, pair_f, pair_g, pair_e0, level_off,
+        level_r0, level_s0, recipe_off, seg_off, acc_slot, seg_pair, unrec_list, parity, total;
 };
 
 static inline DecodeLayout decode_layout(const fs_code *c) {
@@ -82,10 +87,9 @@ static inline DecodeLayout decode_layout(const fs_code *c) {
     L.front_a = o;    o = fs_align256(o + 4 * (G + 1));
     L.front_b = o;    o = fs_align256(o + 4 * (G + 1));
     L.touched = o;    o = fs_align256(o + 4 * (K + 1));
-    L.lvl_o = o;      o = fs_align256(o + 4 * (K + 1));
-    L.lvl_v = o;      o = fs_align256(o + 4 * (K + 1));
     L.pair_f = o;     o = fs_align256(o + 4 * (K + 1));
     L.pair_g = o;     o = fs_align256(o + 4 * (K + 1));
+    L.pair_e0 = o;    o = fs_align256(o + 4 * (K + 1));
     L.level_off = o;  o = fs_align256(o + 4 * (K + 2));
     L.level_r0 = o;   o = fs_align256(o + 4 * (K + 2));
     L.level_s0 = o;   o = fs_align256(o + 4 * (K + 2));
@@ -93,17 +97,12 @@ static inline DecodeLayout decode_layout(const fs_code *c) {
     L.seg_off = o;    o = fs_align256(o + 4 * (K + 1));
     L.acc_slot = o;   o = fs_align256(o + 4 * (K + 1));
     L.seg_pair = o;   o = fs_align256(o + 4 * (K + (size_t)c->e_con / kRecipeSeg + 2));
-    L.recipe_h = o;   o = fs_align256(o + 4 * ((size_t)c->e_con + 1));
     L.unrec_list = o; o = fs_align256(o + 4 * (K + 1));
     L.parity = o;     o = fs_align256(o + (size_t)c->m * (size_t)c->t);
     L.total = o;
     return L;
 }
 
-// Update workspace: mark[i] = position of data block i in the index list or
-// -1; pmark[j] / cmark[g] flag changed checks / touched coded rows, listed in
-// plist / clist (counts in header words WS_COUNT_A / WS_COUNT_B); delta holds
-// old ^ new per listed block, pdelta the change of each changed parity.
 struct UpdateLayout {
     size_t mark, pmark, cmark, plist, clist, delta, pdelta, total;
 };

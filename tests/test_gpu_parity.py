@@ -228,3 +228,73 @@ def test_zero_coded_rows():
     code.decode(None, None, out, unrec, nun, code.workspace(fs.OP_DECODE))
     torch.cuda.synchronize()
     assert not _host(out).any() and _host(unrec).all() and int(_host(nun)[0]) == 4
+
+
+def _graph_from_rows(b, rows):
+    ptr = np.zeros(len(rows) + 1, np.int32)
+    for j, r in enumerate(rows):
+        ptr[j + 1] = ptr[j] + len(r)
+    idx = np.array([v for r in rows for v in sorted(r)], dtype=np.int32)
+    return gen.Graph(b, 0, len(rows), np.zeros(1, np.int32), np.zeros(0, np.int32), ptr, idx)
+
+
+def _check_plain(g, t, erased, tuning=None):
+    import torch
+    fs = _fs()
+    data = gen.fill_bytes(11, g.b * t).reshape(g.b, t)
+    code = fs.Code(g, t)
+    for knob, value in (tuning or {}).items():
+        code.set_tuning(knob, value)
+    _, cod = oracle.encode(g, data, t)
+    cd = _dev(cod)
+    out = torch.empty((g.b, t), dtype=torch.uint8, device="cuda")
+    unrec = torch.empty(g.b, dtype=torch.uint8, device="cuda")
+    nun = torch.empty(1, dtype=torch.int32, device="cuda")
+    ws = code.workspace(fs.OP_DECODE)
+    code.decode(cd, _dev(erased), out, unrec, nun, ws)
+    want, path = oracle.decode(g, cod, erased, t)
+    torch.cuda.synchronize()
+    assert np.array_equal(_host(unrec), path.unrecovered)
+    assert np.array_equal(_host(out), want)
+    view = code.decode_path(ws)
+    assert view["n_levels"] == path.n_levels
+    assert _path_levels(view) == path.levels()
+    return path
+
+
+def test_wide_level_takes_the_direct_path():
+    """600 degree-1 rows: one level of 600 pairs, more than a shared-memory
+    stage holds, so the payload reads the path straight from global memory."""
+    b = 600
+    rows = [[j] for j in range(b)] + [[j, (j + 1) % b] for j in range(40)]
+    g = _graph_from_rows(b, rows)
+    erased = np.zeros(len(rows), np.uint8)
+    erased[gen.sample_indices(b, 30, 5)] = 1
+    path = _check_plain(g, 48, erased)
+    assert max(len(s) for s in path.levels()) > 256
+
+
+def test_long_chain_takes_the_direct_path():
+    """Row 0 = {0}, row j = {j-1, j}: one symbol per level, 1100 levels."""
+    b = 1100
+    rows = [[0]] + [[j - 1, j] for j in range(1, b)]
+    g = _graph_from_rows(b, rows)
+    path = _check_plain(g, 32, np.zeros(b, np.uint8))
+    assert path.n_levels == b
+
+
+@pytest.mark.parametrize("knob,value", [(1, 2), (1, 4), (3, 1), (2, 1), (4, 0), (5, 1)])
+def test_tuning_knobs_leave_results_unchanged(knob, value):
+    """Payload CTAs per SM, check accumulators on, one gather CTA per SM,
+    general (not compact) decoding schedule, gather prefetch on."""
+    import torch
+    fs = _fs()
+    case = Case(1500, 60, 2000, 4096 + 32, gen.DIST_FINITE40)
+    case.code.set_tuning(knob, value)
+    _, p, cd = case.encode_gpu()
+    par, cod = oracle.encode(case.g, case.data, case.t)
+    assert np.array_equal(_host(p), par) and np.array_equal(_host(cd), cod)
+    for s in range(2):
+        _check_decode(case, cod, cd, _erased(case.n, 0.15, gen.SEED_ERASE + (s << 20)))
+    with pytest.raises(fs.FounsureError):
+        case.code.set_tuning(knob, 99)
