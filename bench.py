@@ -252,10 +252,7 @@ def run_gpu(args):
         tuning[fs.TUNE_PEEL_CTAS] = args.peel_ctas
     if args.gather_ctas:
         tuning[fs.TUNE_GATHER_CTAS] = args.gather_ctas
-    if args.check_acc:
-        tuning[fs.TUNE_CHECK_ACC] = 1
-    if args.prefetch:
-        tuning[fs.TUNE_PEEL_PREFETCH] = 1
+
     st = Stripe(rank, max(args.steps, 1) + args.warmup, device, tuning,
                 overlap=not args.serial_schedule)
     torch.cuda.synchronize()
@@ -332,9 +329,7 @@ def run_gpu(args):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "schedule_beside_encode": not args.serial_schedule,
                    "tuning": {"peel_ctas": args.peel_ctas or 1,
-                              "gather_ctas": args.gather_ctas or 8,
-                              "check_acc": args.check_acc,
-                              "prefetch": args.prefetch}},
+                              "gather_ctas": args.gather_ctas or 8}},
         "ops_ms": {k: round(v, 4) for k, v in op_ms.items()},
         "encode_source_gbs": round(B * T / (op_ms["encode"] * 1e-3) / 1e9, 1),
         "decode_source_gbs": round(recovered / ((op_ms["decode_schedule"] +
@@ -451,10 +446,7 @@ def main():
                     help="run the decoding schedule after the encode instead of beside it")
     ap.add_argument("--peel-ctas", type=int, default=0, help="tuning knob (1..8)")
     ap.add_argument("--gather-ctas", type=int, default=0, help="tuning knob (1..16)")
-    ap.add_argument("--check-acc", action="store_true",
-                    help="tuning knob: decode checks from shared-memory accumulators")
-    ap.add_argument("--prefetch", action="store_true",
-                    help="tuning knob: prefetch gathered blocks into L2")
+
     ap.add_argument("--block-bytes", type=int, default=65536,
                     help="block size t (default 65536; smaller only for profiling captures)")
     args = ap.parse_args()

@@ -105,14 +105,6 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
  *                        (1..8; default 1)
  *   FS_TUNE_GATHER_CTAS  resident CTAs per SM of the gather kernels
  *                        (1..16; default 8)
- *   FS_TUNE_CHECK_ACC    1: the payload peel keeps a running XOR of the
- *                        recovered members of every precode check in shared
- *                        memory (when it fits), so a check decodes its last
- *                        unknown without gathering its row; 0 (default):
- *                        gather the row
- *   FS_TUNE_PEEL_PREFETCH 1: the payload peel prefetches the blocks the
- *                        next level gathers into L2; 0 (default): only the
- *                        coded payloads
  *   FS_TUNE_DPG_COMPACT  1 (default): the decoding schedule runs with 16-bit
  *                        indices and the whole graph in shared memory when
  *                        the code has at most 65536 intermediates and
@@ -121,9 +113,7 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
  * thread-safe against concurrent hot calls on the same code. */
 #define FS_TUNE_PEEL_CTAS   1
 #define FS_TUNE_GATHER_CTAS 2
-#define FS_TUNE_CHECK_ACC   3
-#define FS_TUNE_DPG_COMPACT 4
-#define FS_TUNE_PEEL_PREFETCH 5
+#define FS_TUNE_DPG_COMPACT 3
 fs_status fs_code_set_tuning(fs_code *code, int knob, int value);
 
 /* Bytes of caller-provided device workspace that op needs. n_items is the

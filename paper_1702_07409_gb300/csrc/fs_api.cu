@@ -52,8 +52,8 @@ void free_code(fs_code *c) {
     cudaFree(c->pre_idx);
     cudaFree(c->var_ptr);
     cudaFree(c->var_idx);
-    cudaFree(c->chk_ptr);
-    cudaFree(c->chk_idx);
+    cudaFree(c->con_ptr4);
+    cudaFree(c->con_idx4);
     free(c);
 }
 
@@ -90,7 +90,8 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     const int64_t e_lt = lt->row_ptr[n];
     const int64_t e_pre = precode ? precode->row_ptr[m] : 0;
     const int64_t e_con = e_lt + e_pre + m;
-    if (e_con >= INT32_MAX || (int64_t)n + m >= INT32_MAX) return FS_ERR_INVALID;
+    if (e_con + 3 * ((int64_t)n + m) >= INT32_MAX || (int64_t)n + m >= INT32_MAX)
+        return FS_ERR_INVALID;
 
     const int32_t k_int = b + m, n_con = n + m;
     // joint constraint graph: coded rows, then checks (members + own parity)
@@ -126,20 +127,15 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
         for (int32_t g = 0; g < n_con; ++g)
             for (int32_t e = con_ptr[g]; e < con_ptr[g + 1]; ++e) var_idx[fill[con_idx[e]]++] = g;
     }
-    // checks containing each intermediate: data v -> its precode checks
-    // (ascending), parity b + j -> j
-    std::vector<int32_t> chk_ptr((size_t)k_int + 1, 0), chk_idx((size_t)(e_pre + m));
-    for (int64_t e = 0; e < e_pre; ++e) chk_ptr[precode->col_idx[e] + 1]++;
-    for (int32_t j = 0; j < m; ++j) chk_ptr[b + j + 1] = 1;
-    for (int32_t v = 0; v < k_int; ++v) chk_ptr[v + 1] += chk_ptr[v];
-    {
-        std::vector<int32_t> fill(chk_ptr.begin(), chk_ptr.end() - 1);
-        for (int32_t j = 0; j < m; ++j) {
-            for (int32_t e = precode->row_ptr[j]; e < precode->row_ptr[j + 1]; ++e)
-                chk_idx[fill[precode->col_idx[e]]++] = j;
-            chk_idx[fill[b + j]++] = j;
-        }
-    }
+    // rows padded to a multiple of 4 entries with -1, each starting on a
+    // 16-byte boundary, so the payload kernel stages a row with one bulk copy
+    std::vector<int32_t> con_ptr4((size_t)n_con + 1, 0);
+    for (int32_t g = 0; g < n_con; ++g)
+        con_ptr4[g + 1] = con_ptr4[g] + ((con_ptr[g + 1] - con_ptr[g] + 3) & ~3);
+    std::vector<int32_t> con_idx4((size_t)con_ptr4[n_con], -1);
+    for (int32_t g = 0; g < n_con; ++g)
+        for (int32_t e = con_ptr[g]; e < con_ptr[g + 1]; ++e)
+            con_idx4[(size_t)con_ptr4[g] + (e - con_ptr[g])] = con_idx[e];
     std::vector<int32_t> pre_ptr((size_t)m + 1, 0), pre_idx((size_t)e_pre);
     for (int32_t j = 0; j <= m && precode; ++j) pre_ptr[j] = precode->row_ptr[j];
     if (e_pre) memcpy(pre_idx.data(), precode->col_idx, sizeof(int32_t) * (size_t)e_pre);
@@ -159,11 +155,10 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     c->e_con = e_con;
     c->max_con_deg = max_con_deg;
     c->max_var_deg = max_var_deg;
+    c->e_con4 = (int64_t)con_ptr4[n_con];
     c->peel_ctas = 1;
     c->gather_ctas = 8;
-    c->peel_chk_acc = 0;
     c->dpg_compact = 1;
-    c->peel_prefetch = 0;
     cudaError_t e = cudaGetDevice(&c->device);
     int v = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c->device);
@@ -178,8 +173,8 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     if (e == cudaSuccess) e = upload(&c->pre_idx, pre_idx);
     if (e == cudaSuccess) e = upload(&c->var_ptr, var_ptr);
     if (e == cudaSuccess) e = upload(&c->var_idx, var_idx);
-    if (e == cudaSuccess) e = upload(&c->chk_ptr, chk_ptr);
-    if (e == cudaSuccess) e = upload(&c->chk_idx, chk_idx);
+    if (e == cudaSuccess) e = upload(&c->con_ptr4, con_ptr4);
+    if (e == cudaSuccess) e = upload(&c->con_idx4, con_idx4);
     if (e != cudaSuccess) {
         free_code(c);
         return e == cudaErrorMemoryAllocation ? FS_ERR_NOMEM : FS_ERR_CUDA;
@@ -211,17 +206,9 @@ FS_API fs_status fs_code_set_tuning(fs_code *c, int knob, int value) {
             if (value < 1 || value > 8) return FS_ERR_INVALID;
             c->peel_ctas = value;
             return FS_OK;
-        case FS_TUNE_CHECK_ACC:
-            if (value != 0 && value != 1) return FS_ERR_INVALID;
-            c->peel_chk_acc = value;
-            return FS_OK;
         case FS_TUNE_DPG_COMPACT:
             if (value != 0 && value != 1) return FS_ERR_INVALID;
             c->dpg_compact = value;
-            return FS_OK;
-        case FS_TUNE_PEEL_PREFETCH:
-            if (value != 0 && value != 1) return FS_ERR_INVALID;
-            c->peel_prefetch = value;
             return FS_OK;
         case FS_TUNE_GATHER_CTAS:
             if (value < 1 || value > 16) return FS_ERR_INVALID;

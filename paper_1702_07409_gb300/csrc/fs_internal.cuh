@@ -25,21 +25,20 @@ struct fs_code {
     int32_t *con_ptr;     // [n_con + 1]
     int32_t *con_idx;     // [e_con]
     int32_t *con_xs;      // [n_con] XOR of the variable indices of each constraint
+    int32_t *con_ptr4;    // [n_con + 1] row starts of con_idx4 (multiples of 4)
+    int32_t *con_idx4;    // rows of the joint graph padded to 16 bytes with -1
+    int64_t e_con4;       // entries of con_idx4
     int32_t *pre_ptr;     // [m + 1]   precode rows (members only)
     int32_t *pre_idx;     // [e_pre]
     int32_t *var_ptr;     // [k_int + 1] transpose of the joint graph
     int32_t *var_idx;     // [e_con]
-    int32_t *chk_ptr;     // [k_int + 1] checks containing each intermediate
-    int32_t *chk_idx;     // [e_pre + m]  (data: its precode checks; parity b+j: j)
     int device;
     int num_sms;
     size_t smem_optin;    // max dynamic shared memory per block
     // tuning knobs (fs_code_set_tuning); they never change results
     int peel_ctas;        // payload-peel CTAs per SM (slice width follows)
     int gather_ctas;      // resident CTAs per SM for the gather kernels
-    int peel_chk_acc;     // 1: checks decode from shared-memory accumulators
     int dpg_compact;      // 1: symbolic peel in the compact shared-memory form when it fits
-    int peel_prefetch;    // 1: the payload peel prefetches gathered blocks into L2
 };
 
 constexpr int kRecipeSeg = 8;  // recipe entries one payload thread gathers at once
@@ -61,19 +60,23 @@ enum {
 };
 
 // Decode workspace. The DPG state arrays (res .. known) are a spill area used
-// only when they do not fit in shared memory. The decoding path is written as
-// level_off[l] (first pair of level l), level_r0[l] (first recipe entry of
-// level l), level_s0[l] (first gather segment of level l), and per pair p:
-// pair_f, pair_g, pair_e0 (first entry of the row of pair_g in the joint
-// graph), recipe_off (first entry of its recipe), seg_off (first of its
-// gather segments), acc_slot (for a pair with several segments, its rank
-// among such pairs of its level, else -1); per segment: seg_pair (its pair,
-// counted from the first pair of the level). The recipe of pair p is the row
-// of constraint pair_g[p] (pair_f[p] included; the payload kernel skips it);
-// it is gathered in segments of at most kRecipeSeg entries.
+// only when they do not fit in shared memory. The decoding path is written
+// for the C API as level_off[l] (first pair of level l) and pair_f / pair_g,
+// and for the payload kernel as
+//   level_tab[l] = {first pair, pairs, first segment (a multiple of 4),
+//                   segments}
+//   pair_rec[p]  = {f, g, ro, slot, e4, deg4, so, nseg}: ro = offset of its
+//                  recipe in the level's recipe area, slot = its
+//                  accumulator among the level's multi-segment pairs or -1,
+//                  e4 / deg4 = its row in con_idx4, so / nseg = its first
+//                  segment (level-relative) and segment count
+//   seg_pair[s]  = pair of segment s (level-relative)
+// The recipe of a pair is its padded row (f included and -1 padding, both
+// skipped by the payload), gathered in segments of kRecipeSeg entries. All
+// per-level ranges are 16-byte aligned so one bulk copy stages each.
 struct DecodeLayout {
-    size_t res, xs, best, known, front_a, front_b, touched, pair_f, pair_g, pair_e0, level_off,
-        level_r0, level_s0, recipe_off, seg_off, acc_slot, seg_pair, unrec_list, parity, total;
+    size_t res, xs, best, known, front_a, front_b, touched, pair_f, pair_g, pair_rec, level_off,
+        level_tab, seg_pair, unrec_list, parity, total;
 };
 
 static inline DecodeLayout decode_layout(const fs_code *c) {
@@ -89,14 +92,10 @@ static inline DecodeLayout decode_layout(const fs_code *c) {
     L.touched = o;    o = fs_align256(o + 4 * (K + 1));
     L.pair_f = o;     o = fs_align256(o + 4 * (K + 1));
     L.pair_g = o;     o = fs_align256(o + 4 * (K + 1));
-    L.pair_e0 = o;    o = fs_align256(o + 4 * (K + 1));
+    L.pair_rec = o;   o = fs_align256(o + 32 * (K + 1));
     L.level_off = o;  o = fs_align256(o + 4 * (K + 2));
-    L.level_r0 = o;   o = fs_align256(o + 4 * (K + 2));
-    L.level_s0 = o;   o = fs_align256(o + 4 * (K + 2));
-    L.recipe_off = o; o = fs_align256(o + 4 * (K + 1));
-    L.seg_off = o;    o = fs_align256(o + 4 * (K + 1));
-    L.acc_slot = o;   o = fs_align256(o + 4 * (K + 1));
-    L.seg_pair = o;   o = fs_align256(o + 4 * (K + (size_t)c->e_con / kRecipeSeg + 2));
+    L.level_tab = o;  o = fs_align256(o + 16 * (K + 2));
+    L.seg_pair = o;   o = fs_align256(o + 4 * (5 * K + (size_t)c->e_con4 / kRecipeSeg + 8));
     L.unrec_list = o; o = fs_align256(o + 4 * (K + 1));
     L.parity = o;     o = fs_align256(o + (size_t)c->m * (size_t)c->t);
     L.total = o;

@@ -283,10 +283,10 @@ def test_long_chain_takes_the_direct_path():
     assert path.n_levels == b
 
 
-@pytest.mark.parametrize("knob,value", [(1, 2), (1, 4), (3, 1), (2, 1), (4, 0), (5, 1)])
+@pytest.mark.parametrize("knob,value", [(1, 2), (1, 4), (2, 1), (3, 0)])
 def test_tuning_knobs_leave_results_unchanged(knob, value):
-    """Payload CTAs per SM, check accumulators on, one gather CTA per SM,
-    general (not compact) decoding schedule, gather prefetch on."""
+    """Payload CTAs per SM, one gather CTA per SM, general (not compact)
+    decoding schedule."""
     import torch
     fs = _fs()
     case = Case(1500, 60, 2000, 4096 + 32, gen.DIST_FINITE40)
