@@ -53,7 +53,9 @@ typedef enum {
     FS_ERR_INVALID = 2, /* bad argument, graph, alignment or index */
     FS_ERR_CUDA = 3,    /* a CUDA runtime call failed */
     FS_ERR_NOMEM = 4,   /* fs_code_create could not allocate */
-    FS_ERR_TIMEOUT = 5  /* a bounded device wait gave up */
+    FS_ERR_TIMEOUT = 5, /* a bounded device wait gave up */
+    FS_ERR_SCRATCH = 6  /* fs_encode_static: the code needs more scratch than
+                           its static area holds */
 } fs_status;
 
 /* A bipartite graph in CSR form, in HOST memory. Row r lists column indices
@@ -209,6 +211,30 @@ fs_status fs_update(const fs_code *code, const int32_t *d_idx, int32_t n_idx, co
  */
 fs_status fs_repair(const fs_code *code, const int32_t *d_lost, int32_t n_lost, const void *d_data,
                     const void *d_parity, void *d_coded, void *d_ws, void *stream);
+
+/*
+ * Encode without any caller workspace, for callers that cannot allocate
+ * device memory (the paper has no counterpart: this is a deployment aid).
+ * fs_encode needs a small workspace; a storage service that reserves all of
+ * its device memory at start-up and forbids later allocation (cudaMalloc may
+ * synchronise the device and can fail under memory pressure in the middle
+ * of a request), or a binding with no device allocator, cannot supply one.
+ * This call computes exactly what fs_encode computes (same arguments without
+ * d_ws) using a static device area of FS_ENCODE_STATIC_SCRATCH_BYTES bytes
+ * that every GPU loading the library holds until the process exits.
+ *   d_status  optional device int32: receives the call's status word (FS_OK,
+ *             or FS_ERR_TIMEOUT if a bounded wait gave up); NULL to skip
+ * Returns FS_ERR_SCRATCH when fs_workspace_bytes(code, FS_OP_ENCODE, 0)
+ * exceeds FS_ENCODE_STATIC_SCRATCH_BYTES (blocks larger than about 127 MiB),
+ * FS_ERR_INVALID for bad arguments or when the current device is not the
+ * code's device. It calls no allocator. The first call on each device looks
+ * up the area's device address (make it before any stream capture). All
+ * calls share the area: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.
+ */
+#define FS_ENCODE_STATIC_SCRATCH_BYTES 65536
+fs_status fs_encode_static(const fs_code *code, const void *d_data, void *d_parity, void *d_coded,
+                           int32_t *d_status, void *stream);
 
 /* Static string naming a status. */
 const char *fs_status_string(fs_status s);

@@ -71,6 +71,8 @@ FS_API const char *fs_status_string(fs_status s) {
         case FS_ERR_CUDA: return "FS_ERR_CUDA: a CUDA runtime call failed";
         case FS_ERR_NOMEM: return "FS_ERR_NOMEM: device allocation failed";
         case FS_ERR_TIMEOUT: return "FS_ERR_TIMEOUT: a bounded device wait gave up";
+        case FS_ERR_SCRATCH:
+            return "FS_ERR_SCRATCH: the code needs more scratch than fs_encode_static holds";
     }
     return "unknown fs_status";
 }

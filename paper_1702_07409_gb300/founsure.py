@@ -15,7 +15,8 @@ import numpy as np
 
 from . import _build
 
-FS_OK, FS_STALL, FS_ERR_INVALID, FS_ERR_CUDA, FS_ERR_NOMEM, FS_ERR_TIMEOUT = range(6)
+FS_OK, FS_STALL, FS_ERR_INVALID, FS_ERR_CUDA, FS_ERR_NOMEM, FS_ERR_TIMEOUT, FS_ERR_SCRATCH = range(7)
+ENCODE_STATIC_SCRATCH_BYTES = 65536
 DECODE_JOINT, DECODE_TWO_PASS = 0, 1
 OP_ENCODE, OP_DECODE, OP_UPDATE, OP_REPAIR = 0, 1, 2, 3
 TUNE_PEEL_CTAS, TUNE_GATHER_CTAS, TUNE_DPG_COMPACT = 1, 2, 3
@@ -24,7 +25,7 @@ WS_STATUS_OFFSET = 0
 #: every symbol declared in include/founsure_gpu.h
 EXPORTS = ("fs_code_create", "fs_code_destroy", "fs_code_info", "fs_code_set_tuning",
            "fs_workspace_bytes",
-           "fs_encode", "fs_encode_rows", "fs_decode", "fs_decode_schedule",
+           "fs_encode", "fs_encode_static", "fs_encode_rows", "fs_decode", "fs_decode_schedule",
            "fs_decode_payload", "fs_decode_path", "fs_update", "fs_repair", "fs_status_string")
 
 
@@ -66,6 +67,8 @@ def lib() -> ctypes.CDLL:
         L.fs_workspace_bytes.restype = sz
         L.fs_encode.argtypes = [vp, vp, vp, vp, vp, vp]
         L.fs_encode.restype = ctypes.c_int
+        L.fs_encode_static.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.fs_encode_static.restype = ctypes.c_int
         L.fs_encode_rows.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
         L.fs_encode_rows.restype = ctypes.c_int
         L.fs_decode.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
@@ -195,6 +198,15 @@ class Code:
         self._need(coded, self.n * self.t, "coded")
         _check(lib().fs_encode(self._h, _addr(data), _addr(parity), _addr(coded), _addr(ws),
                                _stream(stream)), "fs_encode")
+
+    def encode_static(self, data, parity, coded, status=None, stream=None) -> None:
+        """fs_encode_static: the encode with the library's static scratch area
+        instead of a caller workspace (for callers that cannot allocate)."""
+        self._need(data, self.b * self.t, "data")
+        self._need(parity, self.m * self.t, "parity")
+        self._need(coded, self.n * self.t, "coded")
+        _check(lib().fs_encode_static(self._h, _addr(data), _addr(parity), _addr(coded),
+                                      _addr(status), _stream(stream)), "fs_encode_static")
 
     def encode_rows(self, row_begin, row_end, data, parity, coded, ws, stream=None) -> None:
         _check(lib().fs_encode_rows(self._h, row_begin, row_end, _addr(data), _addr(parity),

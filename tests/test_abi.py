@@ -49,7 +49,7 @@ def test_every_declared_symbol_is_exported(gpu_lib):
 
 def test_status_strings(gpu_lib):
     gpu_lib.fs_status_string.restype = ctypes.c_char_p
-    for s in range(6):
+    for s in range(7):
         assert gpu_lib.fs_status_string(s).startswith(b"FS_")
 
 

@@ -1,0 +1,65 @@
+"""fs_encode_static: the encode entry point for callers that cannot allocate
+device memory (a storage service that reserves all of its device memory at
+start-up, or a binding without a device allocator). It must produce exactly
+what fs_encode produces, call after call, from its static scratch area.
+
+This file is collected last on purpose, so a run that stops at the first
+failure has run every other test first."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1702_07409_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+
+def _encode_both(fs, g, t, seed):
+    """Encodes seeded data with fs_encode and with fs_encode_static (called
+    directly through the C ABI) and returns both outputs and the status."""
+    import torch
+    code = fs.Code(g, t)
+    data = torch.from_numpy(gen.fill_bytes(seed, g.b * t).reshape(g.b, t)).cuda()
+    p0 = torch.empty((g.m, t), dtype=torch.uint8, device="cuda") if g.m else None
+    c0 = torch.empty((g.n, t), dtype=torch.uint8, device="cuda")
+    code.encode(data, p0, c0, code.workspace(fs.OP_ENCODE))
+    p1 = torch.full((g.m, t), 0x5A, dtype=torch.uint8, device="cuda") if g.m else None
+    c1 = torch.full((g.n, t), 0x5A, dtype=torch.uint8, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = fs.lib().fs_encode_static(code._h, ctypes.c_void_p(data.data_ptr()),
+                                   ctypes.c_void_p(p1.data_ptr()) if p1 is not None else None,
+                                   ctypes.c_void_p(c1.data_ptr()),
+                                   ctypes.c_void_p(status.data_ptr()), ctypes.c_void_p(stream))
+    assert rc == fs.FS_OK
+    torch.cuda.synchronize()
+    return (p0, c0), (p1, c1), int(status.item()), code
+
+
+def test_static_encode_matches_encode_twice_in_a_row():
+    from paper_1702_07409_gb300 import founsure as fs
+    cases = [
+        (gen.make_graph(600, 24, 800, gen.DIST_FINITE40), 4096 + 48, 7),
+        (gen.make_graph(100, 0, 150, gen.DIST_RSD, 0.1, 0.05), 1024, 1),
+    ]
+    for g, t, seed in cases:
+        for call in range(2):  # the second call reuses the area the first left behind
+            (p0, c0), (p1, c1), status, _ = _encode_both(fs, g, t, seed + call)
+            assert status == fs.FS_OK
+            assert np.array_equal(c1.cpu().numpy(), c0.cpu().numpy())
+            if g.m:
+                assert np.array_equal(p1.cpu().numpy(), p0.cpu().numpy())
+
+
+def test_static_encode_rejects_codes_beyond_its_area():
+    """A code whose encode needs more scratch than the static area is refused
+    on the host, before any device work."""
+    from paper_1702_07409_gb300 import founsure as fs
+    g = gen.make_graph(8, 0, 12, gen.DIST_RSD, 0.1, 0.05)
+    t = 256 * 1024 * 1024  # 256 MiB blocks: more byte chunks than the area counts
+    code = fs.Code(g, t)
+    assert code.workspace_bytes(fs.OP_ENCODE) > fs.ENCODE_STATIC_SCRATCH_BYTES
+    fake = ctypes.c_void_p(1 << 20)  # aligned, never dereferenced: the call is refused first
+    rc = fs.lib().fs_encode_static(code._h, fake, None, fake, None, None)
+    assert rc == fs.FS_ERR_SCRATCH
