@@ -127,6 +127,10 @@ __device__ __forceinline__ int find_slot(const int32_t *off, int n, int32_t x) {
     return lo;
 }
 
+__device__ __forceinline__ uint32_t smem_addr_u(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
 template <typename T>
 __device__ __forceinline__ T *place(unsigned char *smem, int32_t off, T *global) {
     return off >= 0 ? reinterpret_cast<T *>(smem + off) : global;
@@ -408,19 +412,33 @@ DpgPlace plan_dpg(const fs_code *c) {
 }
 
 struct DpgCompactPlace {
-    int32_t best, pk, front, next, touched, known, cptr4, vptr, vidx, ok, lvl_v, deg, bytes;
+    int32_t best, pk, front, next, touched, known, cptr4, vptr, vidx, ok, lvl_v, deg, slots,
+        bytes;
 };
+
+constexpr int kSlotCap = 4096;        // adjacency slots of one level mapped without search
+constexpr uint32_t kClaim = 0x80000000u;  // pk bit: constraint already appended to a frontier
+
+__device__ __forceinline__ void red_xor_shared(uint32_t *p, uint32_t v) {
+    asm volatile("red.shared.xor.b32 [%0], %1;\n" ::"r"(smem_addr_u(p)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_add_shared(uint32_t *p, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;\n" ::"r"(smem_addr_u(p)), "r"(v) : "memory");
+}
 
 __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCompactPlace pl) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int4 s_warp4[32];
-    __shared__ int s_nf, s_nt, s_nnext, s_cnt, s_cnt_data;
+    // list counters indexed by level parity, so a level never resets the
+    // counters it is still reading
+    __shared__ int s_nt[2], s_nnext[2], s_nf0, s_cnt, s_cnt_data;
     constexpr uint32_t kE = 0xffffffffu;
 
     const int tid = threadIdx.x, T = blockDim.x;
     const int32_t K = a.k_int, G = a.n_con;
     uint32_t *best = reinterpret_cast<uint32_t *>(smem + pl.best);
-    uint32_t *pk = reinterpret_cast<uint32_t *>(smem + pl.pk);
+    uint32_t *pk = reinterpret_cast<uint32_t *>(smem + pl.pk);  // claim | res << 16 | xs
     uint16_t *front = reinterpret_cast<uint16_t *>(smem + pl.front);
     uint16_t *next = reinterpret_cast<uint16_t *>(smem + pl.next);
     uint16_t *touched = reinterpret_cast<uint16_t *>(smem + pl.touched);
@@ -431,6 +449,7 @@ __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCo
     uint16_t *deg = reinterpret_cast<uint16_t *>(smem + pl.deg);
     uint8_t *ok = smem + pl.ok;
     int32_t *lvl_v = reinterpret_cast<int32_t *>(smem + pl.lvl_v);
+    uint16_t *slots = reinterpret_cast<uint16_t *>(smem + pl.slots);  // [kSlotCap]
 
     if (tid == 0) a.hdr[WS_STATUS] = FS_OK;
     for (int32_t g = tid; g <= G; g += T) cptr4[g] = __ldg(a.con_ptr4 + g);
@@ -448,40 +467,47 @@ __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCo
         ok[g] = (g < a.n) ? (a.erased[g] == 0) : 1;
     }
     int stage = a.two_pass ? 0 : -1;
-    if (tid == 0) s_nf = 0;
+    if (tid == 0) {
+        s_nf0 = 0;
+        s_nt[0] = s_nt[1] = 0;
+        s_nnext[0] = s_nnext[1] = 0;
+    }
     __syncthreads();
     for (int32_t g = tid; g < G; g += T)
-        if (usable(a, ok, g, stage) && (pk[g] >> 16) == 1) front[append_slot(&s_nf)] = (uint16_t)g;
+        if (usable(a, ok, g, stage) && (pk[g] >> 16) == 1) {
+            pk[g] |= kClaim;
+            front[append_slot(&s_nf0)] = (uint16_t)g;
+        }
     __syncthreads();
+    int nf = s_nf0;
 
     LevelCursor cur;
     for (;;) {
-        const int nf = s_nf;
-        if (tid == 0) {
-            s_nt = 0;
-            s_nnext = 0;
-        }
-        __syncthreads();
+        const int par = cur.level & 1;
         // A: frontier constraints bid for their single unknown
         for (int i = tid; i < nf; i += T) {
             const int32_t g = front[i];
             const uint32_t w = pk[g];
-            if ((w >> 16) != 1) continue;  // its unknown was decoded by another constraint
+            if (((w >> 16) & 0x7fffu) != 1) continue;  // its unknown was decoded by another constraint
             const int32_t f = (int32_t)(w & 0xffffu);
             const uint32_t key = ((uint32_t)deg[g] << 16) | (uint32_t)g;
-            if (atomicMin(best + f, key) == kE) touched[append_slot(&s_nt)] = (uint16_t)f;
+            if (atomicMin(best + f, key) == kE) touched[append_slot(&s_nt[par])] = (uint16_t)f;
         }
         __syncthreads();
-        const int nt = s_nt;
+        const int nt = s_nt[par];
         if (nt == 0) {
             if (stage != 0) break;
             // two-pass: the coded rows reached their fixpoint; peel the checks
             stage = 1;
-            if (tid == 0) s_nf = 0;
+            if (tid == 0) s_nf0 = 0;
             __syncthreads();
             for (int32_t g = a.n + tid; g < G; g += T)
-                if ((pk[g] >> 16) == 1) front[append_slot(&s_nf)] = (uint16_t)g;
+                if (((pk[g] >> 16) & 0x7fffu) == 1) {
+                    pk[g] |= kClaim;
+                    front[append_slot(&s_nf0)] = (uint16_t)g;
+                }
             __syncthreads();
+            nf = s_nf0;
             continue;
         }
         // B: pairs of the level (adjacency slots into lvl_v for step C)
@@ -493,29 +519,54 @@ __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCo
                 *vdeg = vptr[*f + 1] - vptr[*f];
             },
             cptr4, lvl_v, s_warp4);
+        const bool mapped = len.w <= kSlotCap;  // uniform: slots of each pair listed
         for (int i = tid; i < nt; i += T) {
             const int32_t f = touched[i];
             best[f] = kE;
             known[f] = 1;
+            if (mapped)
+                for (int32_t u = lvl_v[i], u1 = lvl_v[i] + vptr[f + 1] - vptr[f]; u < u1; ++u)
+                    slots[u] = (uint16_t)i;
+        }
+        if (tid == 0) {  // the counters the next level appends to (read by now)
+            s_nt[par ^ 1] = 0;
+            s_nnext[par ^ 1] = 0;
         }
         __syncthreads();
-        // C: one thread per adjacency slot (its pair found by binary search)
-        // updates one constraint containing a newly decoded symbol
+        // C1: one thread per adjacency slot: res -= 1 and xs ^= f on one
+        // constraint containing a newly decoded symbol, without waiting for
+        // a result; the slot's constraint is remembered for C2
         for (int32_t u = tid; u < len.w; u += T) {
-            const int i = find_slot(lvl_v, nt, u);
+            const int i = mapped ? (int)slots[u] : find_slot(lvl_v, nt, u);
             const int32_t f = touched[i];
             const int32_t c = vidx[vptr[f] + (u - lvl_v[i])];
-            atomicXor(pk + c, (uint32_t)f);
-            if ((atomicSub(pk + c, 1u << 16) >> 16) == 2 && usable(a, ok, c, stage))
-                next[append_slot(&s_nnext)] = (uint16_t)c;
+            red_xor_shared(pk + c, (uint32_t)f);
+            red_add_shared(pk + c, 0xffff0000u);  // -(1 << 16): decrement res
+            if (mapped) slots[u] = (uint16_t)c;
         }
         __syncthreads();
-        if (tid == 0) s_nf = s_nnext;
+        // C2: a touched constraint left with one unknown joins the next
+        // frontier once (its claim bit is set by the one thread that appends)
+        for (int32_t u = tid; u < len.w; u += T) {
+            int32_t c;
+            if (mapped) {
+                c = slots[u];
+            } else {
+                const int i = find_slot(lvl_v, nt, u);
+                const int32_t f = touched[i];
+                c = vidx[vptr[f] + (u - lvl_v[i])];
+            }
+            const uint32_t w = pk[c];
+            if ((w & kClaim) == 0 && (w >> 16) == 1 && usable(a, ok, c, stage) &&
+                (atomicOr(pk + c, kClaim) & kClaim) == 0)
+                next[append_slot(&s_nnext[par])] = (uint16_t)c;
+        }
+        __syncthreads();
+        nf = s_nnext[par];
         advance(cur, nt, len);
         uint16_t *tmp = front;
         front = next;
         next = tmp;
-        __syncthreads();
     }
     finish_dpg(a, cur, known, &s_cnt, &s_cnt_data);
 }
@@ -526,7 +577,8 @@ DpgCompactPlace plan_dpg_compact(const fs_code *c) {
     DpgCompactPlace p;
     p.bytes = -1;
     const int64_t K = c->k_int, G = c->n_con;
-    if (K > 65536 || G > 65536 || c->max_con_deg > 65535) return p;
+    // 16-bit indices; degrees below 2^15 (bit 31 of the packed word is the claim bit)
+    if (K > 65536 || G > 65536 || c->max_con_deg > 32767) return p;
     int64_t o = 0;
     auto take = [&](int64_t bytes) {
         const int64_t at = o;
@@ -542,6 +594,7 @@ DpgCompactPlace plan_dpg_compact(const fs_code *c) {
     p.next = take(2 * (G + 1));
     p.touched = take(2 * (K + 1));
     p.deg = take(2 * (G + 1));
+    p.slots = take(2 * (int64_t)kSlotCap);
     p.vidx = take(2 * (c->e_con + 1));
     p.known = take(K + 1);
     p.ok = take(G + 1);
