@@ -63,20 +63,23 @@ enum {
 // only when they do not fit in shared memory. The decoding path is written
 // for the C API as level_off[l] (first pair of level l) and pair_f / pair_g,
 // and for the payload kernel as
-//   level_tab[l] = {first pair, pairs, first segment (a multiple of 4),
-//                   segments}
+//   level_tab[2l]   = {first pair, pairs, first segment, segments}
+//   level_tab[2l+1] = {first recipe chunk, recipe chunks, 0, 0}: a chunk is
+//                  4 recipe entries (16 bytes); segment and chunk lists start
+//                  on multiples of 4 entries
 //   pair_rec[p]  = {f, g, ro, slot, e4, deg4, so, nseg}: ro = offset of its
 //                  recipe in the level's recipe area, slot = its
 //                  accumulator among the level's multi-segment pairs or -1,
 //                  e4 / deg4 = its row in con_idx4, so / nseg = its first
 //                  segment (level-relative) and segment count
 //   seg_pair[s]  = pair of segment s (level-relative)
+//   chunk_pair[c] = pair whose recipe holds chunk c (level-relative)
 // The recipe of a pair is its padded row (f included and -1 padding, both
 // skipped by the payload), gathered in segments of kRecipeSeg entries. All
 // per-level ranges are 16-byte aligned so one bulk copy stages each.
 struct DecodeLayout {
     size_t res, xs, best, known, front_a, front_b, touched, pair_f, pair_g, pair_rec, level_off,
-        level_tab, seg_pair, unrec_list, parity, total;
+        level_tab, seg_pair, chunk_pair, unrec_list, parity, total;
 };
 
 static inline DecodeLayout decode_layout(const fs_code *c) {
@@ -94,8 +97,9 @@ static inline DecodeLayout decode_layout(const fs_code *c) {
     L.pair_g = o;     o = fs_align256(o + 4 * (K + 1));
     L.pair_rec = o;   o = fs_align256(o + 32 * (K + 1));
     L.level_off = o;  o = fs_align256(o + 4 * (K + 2));
-    L.level_tab = o;  o = fs_align256(o + 16 * (K + 2));
+    L.level_tab = o;  o = fs_align256(o + 32 * (K + 2));
     L.seg_pair = o;   o = fs_align256(o + 4 * (5 * K + (size_t)c->e_con4 / kRecipeSeg + 8));
+    L.chunk_pair = o; o = fs_align256(o + 4 * (4 * K + (size_t)c->e_con4 / 4 + 8));
     L.unrec_list = o; o = fs_align256(o + 4 * (K + 1));
     L.parity = o;     o = fs_align256(o + (size_t)c->m * (size_t)c->t);
     L.total = o;

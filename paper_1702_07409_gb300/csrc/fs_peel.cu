@@ -19,10 +19,14 @@
 //   rule). Appends to the shared lists are warp-aggregated.
 //   k_dpg_compact (graphs with at most 65536 intermediates and constraints)
 //   keeps every per-level access in shared memory: 16-bit indices, res and
-//   xs packed in one word (res << 16 | xs: a decrement touches only the high
-//   half, the XOR only the low half), 32-bit keys, a shared copy of the
-//   transposed graph, and step C run one thread per adjacency slot. k_dpg is
-//   the general form, with its state spilled to the workspace when needed.
+//   xs packed in one word (claim bit | res << 16 | xs: a decrement touches
+//   only the res field, the XOR only the low half), 32-bit keys and a shared
+//   copy of the transposed graph. Its step C runs one thread per adjacency
+//   slot in two passes: fire-and-forget shared reductions, then plain loads
+//   find the constraints left with one unknown; each claims itself once (a
+//   claim bit) and at once bids for the next level, so step A of a level is
+//   done by the previous level's step C. k_dpg is the general form, with its
+//   state spilled to the workspace when needed.
 //
 // k_peel: the payload. Each CTA owns one slice of L 16-byte words of every
 //   block (about one CTA per SM, so every slice is in flight at once) and
@@ -33,8 +37,8 @@
 //   pair records and segment list of level l+2 with two bulk copies
 //   (cp.async.bulk, completion on an mbarrier; each range is 16-byte
 //   aligned), the padded graph rows (recipes) of level l+1 with 16-byte
-//   cp.async copies spread over all threads, plus an L2 prefetch of level
-//   l+1's coded payloads. A recipe is gathered in segments of kRecipeSeg
+//   cp.async copies spread over all threads (a chunk list names the pair of
+//   each 16-byte chunk), plus an L2 prefetch of level l+1's coded payloads. A recipe is gathered in segments of kRecipeSeg
 //   entries, one thread per (segment, word pair), all loads of a segment in
 //   flight at once; pairs with several segments combine them in
 //   shared-memory accumulators before the block is written.
@@ -46,7 +50,7 @@ namespace cg = cooperative_groups;
 
 namespace {
 
-constexpr int kDpgThreads = 256;
+constexpr int kDpgThreads = 1024;  // fills an SM's registers: no other kernel's CTA shares it
 constexpr int kPeelThreads = 512;
 constexpr int kPeelV = 2;           // 16-byte words per payload item
 constexpr int kPeelLmax = 64;       // largest slice (words) of one payload CTA
@@ -71,10 +75,14 @@ __device__ __forceinline__ int append_slot(int *counter) {
     return grp.shfl(base, 0) + (int)grp.thread_rank();
 }
 
-// Block-wide exclusive prefix sum of four counters at once; *total receives
-// the sums. All threads of the block must call it.
-__device__ int4 block_excl_scan4(int4 x, int4 *total, int4 *s_warp) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+// Exclusive prefix sum of four counters over the first nw warps of the block
+// (the warps holding items); *total receives the sums. Only those warps call
+// it; they meet on named barrier 1. Every warp scans its own lanes,
+// publishes its total in s_warp[buf], and after the barrier sums the totals
+// of the warps before it. Consecutive calls must alternate buf (the other
+// buffer may still be read by slow warps).
+__device__ int4 warps_excl_scan4(int4 x, int4 *total, int4 (*s_warp)[32], int buf, int nw) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int4 v = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -89,31 +97,30 @@ __device__ int4 block_excl_scan4(int4 x, int4 *total, int4 *s_warp) {
             v.w += d;
         }
     }
-    if (lane == 31) s_warp[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        int4 s = lane < nw ? s_warp[lane] : make_int4(0, 0, 0, 0);
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int a = __shfl_up_sync(0xffffffffu, s.x, o);
-            const int b = __shfl_up_sync(0xffffffffu, s.y, o);
-            const int c = __shfl_up_sync(0xffffffffu, s.z, o);
-            const int d = __shfl_up_sync(0xffffffffu, s.w, o);
-            if (lane >= o) {
-                s.x += a;
-                s.y += b;
-                s.z += c;
-                s.w += d;
-            }
-        }
-        s_warp[lane] = s;  // inclusive warp totals
+    if (nw == 1) {
+        *total = make_int4(__shfl_sync(0xffffffffu, v.x, 31), __shfl_sync(0xffffffffu, v.y, 31),
+                           __shfl_sync(0xffffffffu, v.z, 31), __shfl_sync(0xffffffffu, v.w, 31));
+        return make_int4(v.x - x.x, v.y - x.y, v.z - x.z, v.w - x.w);
     }
-    __syncthreads();
-    const int4 before = wid > 0 ? s_warp[wid - 1] : make_int4(0, 0, 0, 0);
-    *total = s_warp[nw - 1];
-    __syncthreads();
-    return make_int4(before.x + v.x - x.x, before.y + v.y - x.y, before.z + v.z - x.z,
-                     before.w + v.w - x.w);
+    if (lane == 31) s_warp[buf][wid] = v;
+    asm volatile("bar.sync 1, %0;\n" ::"r"(nw * 32) : "memory");
+    // lane j holds warp j's total; before = sum over j < wid, all = sum over j < nw
+    const int4 t = lane < nw ? s_warp[buf][lane] : make_int4(0, 0, 0, 0);
+    int4 b = lane < wid ? t : make_int4(0, 0, 0, 0);
+    int4 all = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        b.x += __shfl_xor_sync(0xffffffffu, b.x, o);
+        b.y += __shfl_xor_sync(0xffffffffu, b.y, o);
+        b.z += __shfl_xor_sync(0xffffffffu, b.z, o);
+        b.w += __shfl_xor_sync(0xffffffffu, b.w, o);
+        all.x += __shfl_xor_sync(0xffffffffu, all.x, o);
+        all.y += __shfl_xor_sync(0xffffffffu, all.y, o);
+        all.z += __shfl_xor_sync(0xffffffffu, all.z, o);
+        all.w += __shfl_xor_sync(0xffffffffu, all.w, o);
+    }
+    *total = all;
+    return make_int4(b.x + v.x - x.x, b.y + v.y - x.y, b.z + v.z - x.z, b.w + v.w - x.w);
 }
 
 // Largest i in [0, n) with off[i] <= x, for ascending off[0] <= x.
@@ -150,7 +157,7 @@ struct DpgArgs {
     uint8_t *known;
     int32_t *front_a, *front_b, *touched;
     // outputs
-    int32_t *pair_f, *pair_g, *level_off, *seg_pair, *unrec_list, *hdr;
+    int32_t *pair_f, *pair_g, *level_off, *seg_pair, *chunk_pair, *unrec_list, *hdr;
     int4 *pair_rec, *level_tab;
     uint8_t *unrecovered;
     int32_t *n_unrecovered;
@@ -166,19 +173,26 @@ __device__ __forceinline__ bool usable(const DpgArgs &a, const uint8_t *ok, int3
 
 // Per-level bookkeeping shared by both forms of the symbolic pass.
 struct LevelCursor {
-    int32_t np = 0, level = 0, rb = 0, sb = 0, maxp = 0, maxr = 0, maxs = 0, maxm = 0;
+    int32_t np = 0, level = 0, rb = 0, sb = 0, cb = 0, maxp = 0, maxr = 0, maxs = 0, maxm = 0;
+    int scan_buf = 0;
 };
 
 // Step B of a level: writes the pairs i < nt (pair_of(i) gives f, g and the
-// adjacency count of f) and returns the level's totals. lvl_v (may be null)
-// receives the level-relative adjacency slot of each pair and the total at
-// nt. Called by every thread of the block.
+// adjacency count of f) and stores the level's totals in *s_len (read them
+// after the next block barrier). lvl_v (may be null) receives the
+// level-relative adjacency slot of each pair and the total at nt. Called by
+// every thread; only the warps holding pairs scan.
 template <typename PairOf>
-__device__ int4 emit_level(const DpgArgs &a, const LevelCursor &cur, int nt, PairOf pair_of,
-                           const int32_t *cptr4, int32_t *lvl_v, int4 *s_warp4) {
+__device__ void emit_level(const DpgArgs &a, LevelCursor &cur, int nt, PairOf pair_of,
+                           const int32_t *cptr4, int32_t *lvl_v, int4 (*s_warp4)[32],
+                           int4 *s_len) {
     int4 len = make_int4(0, 0, 0, 0);
     const int32_t sb = cur.sb;
     for (int base = 0; base < nt; base += blockDim.x) {
+        const int nw = (min(nt - base, (int)blockDim.x) + 31) >> 5;  // warps holding pairs
+        const int buf = cur.scan_buf;
+        cur.scan_buf ^= 1;
+        if ((int)(threadIdx.x >> 5) >= nw) continue;
         const int i = base + threadIdx.x;
         int4 cnt = make_int4(0, 0, 0, 0);  // recipe, segments, multi, adjacency
         int32_t f = -1, g = -1;
@@ -191,7 +205,7 @@ __device__ int4 emit_level(const DpgArgs &a, const LevelCursor &cur, int nt, Pai
             cnt.w = vdeg;
         }
         int4 total;
-        const int4 off = block_excl_scan4(cnt, &total, s_warp4);
+        const int4 off = warps_excl_scan4(cnt, &total, s_warp4, buf, nw);
         if (i < nt) {
             const int32_t p = cur.np + i;
             a.pair_f[p] = f;
@@ -200,6 +214,8 @@ __device__ int4 emit_level(const DpgArgs &a, const LevelCursor &cur, int nt, Pai
             a.pair_rec[2 * (size_t)p] = make_int4(f, g, len.x + off.x, cnt.z ? len.z + off.z : -1);
             a.pair_rec[2 * (size_t)p + 1] = make_int4(cptr4[g], cnt.x, so, cnt.y);
             for (int k = 0; k < cnt.y; ++k) a.seg_pair[sb + so + k] = i;
+            const int32_t c0 = cur.cb + ((len.x + off.x) >> 2);
+            for (int k = 0; k < (cnt.x >> 2); ++k) a.chunk_pair[c0 + k] = i;
             if (lvl_v) lvl_v[i] = len.w + off.w;
         }
         len.x += total.x;
@@ -207,12 +223,13 @@ __device__ int4 emit_level(const DpgArgs &a, const LevelCursor &cur, int nt, Pai
         len.z += total.z;
         len.w += total.w;
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {  // warp 0 holds pairs whenever nt > 0
         a.level_off[cur.level] = cur.np;
-        a.level_tab[cur.level] = make_int4(cur.np, nt, sb, len.y);
+        a.level_tab[2 * cur.level] = make_int4(cur.np, nt, sb, len.y);
+        a.level_tab[2 * cur.level + 1] = make_int4(cur.cb, len.x >> 2, 0, 0);
         if (lvl_v) lvl_v[nt] = len.w;
+        *s_len = len;
     }
-    return len;
 }
 
 __device__ __forceinline__ void advance(LevelCursor &cur, int nt, const int4 &len) {
@@ -223,6 +240,7 @@ __device__ __forceinline__ void advance(LevelCursor &cur, int nt, const int4 &le
     cur.np += nt;
     cur.rb += len.x;
     cur.sb += (len.y + 3) & ~3;  // each level's segment list starts 16-byte aligned
+    cur.cb += ((len.x >> 2) + 3) & ~3;  // ... and its chunk list
     ++cur.level;
 }
 
@@ -231,7 +249,8 @@ __device__ void finish_dpg(const DpgArgs &a, const LevelCursor &cur, const uint8
                            int *s_cnt, int *s_cnt_data) {
     if (threadIdx.x == 0) {
         a.level_off[cur.level] = cur.np;
-        a.level_tab[cur.level] = make_int4(cur.np, 0, cur.sb, 0);
+        a.level_tab[2 * cur.level] = make_int4(cur.np, 0, cur.sb, 0);
+        a.level_tab[2 * cur.level + 1] = make_int4(cur.cb, 0, 0, 0);
         a.hdr[WS_N_LEVELS] = cur.level;
         a.hdr[WS_N_PAIRS] = cur.np;
         a.hdr[WS_STAGED] = (cur.maxp <= kStagePairs && cur.maxr <= kStageRecipe &&
@@ -267,7 +286,8 @@ struct DpgPlace {
 
 __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg(DpgArgs a, DpgPlace pl) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int4 s_warp4[32];
+    __shared__ int4 s_warp4[2][32];
+    __shared__ int4 s_len;
     __shared__ int s_nf, s_nt, s_nnext, s_cnt, s_cnt_data;
 
     const int tid = threadIdx.x, T = blockDim.x;
@@ -343,20 +363,21 @@ __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg(DpgArgs a, DpgPlace pl) 
             continue;
         }
         // B: pairs of the level
-        const int4 len = emit_level(
+        emit_level(
             a, cur, nt,
             [&](int i, int32_t *f, int32_t *g, int32_t *vdeg) {
                 *f = touched[i];
                 *g = (int32_t)(best[*f] & 0xffffffffull);
                 *vdeg = 0;
             },
-            cptr4, nullptr, s_warp4);
+            cptr4, nullptr, s_warp4, &s_len);
         for (int i = tid; i < nt; i += T) {
             const int32_t f = touched[i];
             best[f] = kEmpty;
             known[f] = 1;
         }
         __syncthreads();
+        const int4 len = s_len;
         // C: one thread per pair updates the constraints containing its symbol
         for (int i = tid; i < nt; i += T) {
             const int32_t f = touched[i];
@@ -429,19 +450,18 @@ __device__ __forceinline__ void red_add_shared(uint32_t *p, uint32_t v) {
 
 __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCompactPlace pl) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int4 s_warp4[32];
-    // list counters indexed by level parity, so a level never resets the
-    // counters it is still reading
-    __shared__ int s_nt[2], s_nnext[2], s_nf0, s_cnt, s_cnt_data;
+    __shared__ int4 s_warp4[2][32];
+    __shared__ int4 s_len;
+    // symbols of the next level, by level parity (a level reads one list
+    // while its step C2 fills the other)
+    __shared__ int s_nt[2], s_cnt, s_cnt_data;
     constexpr uint32_t kE = 0xffffffffu;
 
     const int tid = threadIdx.x, T = blockDim.x;
     const int32_t K = a.k_int, G = a.n_con;
     uint32_t *best = reinterpret_cast<uint32_t *>(smem + pl.best);
     uint32_t *pk = reinterpret_cast<uint32_t *>(smem + pl.pk);  // claim | res << 16 | xs
-    uint16_t *front = reinterpret_cast<uint16_t *>(smem + pl.front);
-    uint16_t *next = reinterpret_cast<uint16_t *>(smem + pl.next);
-    uint16_t *touched = reinterpret_cast<uint16_t *>(smem + pl.touched);
+    uint16_t *touched2 = reinterpret_cast<uint16_t *>(smem + pl.front);  // [2][K + 1]
     uint8_t *known = smem + pl.known;
     int32_t *cptr4 = reinterpret_cast<int32_t *>(smem + pl.cptr4);
     int32_t *vptr = reinterpret_cast<int32_t *>(smem + pl.vptr);
@@ -450,6 +470,17 @@ __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCo
     uint8_t *ok = smem + pl.ok;
     int32_t *lvl_v = reinterpret_cast<int32_t *>(smem + pl.lvl_v);
     uint16_t *slots = reinterpret_cast<uint16_t *>(smem + pl.slots);  // [kSlotCap]
+
+    // A constraint c with one unknown left joins the bidding once: the
+    // thread that sets its claim bit bids key = (degree, c) for its unknown;
+    // the first bid for a symbol lists the symbol for the level.
+    auto claim_and_bid = [&](int32_t c, int list) {
+        if ((atomicOr(pk + c, kClaim) & kClaim) != 0) return;
+        const int32_t f = (int32_t)(pk[c] & 0xffffu);
+        const uint32_t key = ((uint32_t)deg[c] << 16) | (uint32_t)c;
+        if (atomicMin(best + f, key) == kE)
+            touched2[(size_t)list * (K + 1) + append_slot(&s_nt[list])] = (uint16_t)f;
+    };
 
     if (tid == 0) a.hdr[WS_STATUS] = FS_OK;
     for (int32_t g = tid; g <= G; g += T) cptr4[g] = __ldg(a.con_ptr4 + g);
@@ -467,72 +498,53 @@ __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCo
         ok[g] = (g < a.n) ? (a.erased[g] == 0) : 1;
     }
     int stage = a.two_pass ? 0 : -1;
-    if (tid == 0) {
-        s_nf0 = 0;
-        s_nt[0] = s_nt[1] = 0;
-        s_nnext[0] = s_nnext[1] = 0;
-    }
+    if (tid == 0) s_nt[0] = s_nt[1] = 0;
     __syncthreads();
     for (int32_t g = tid; g < G; g += T)
-        if (usable(a, ok, g, stage) && (pk[g] >> 16) == 1) {
-            pk[g] |= kClaim;
-            front[append_slot(&s_nf0)] = (uint16_t)g;
-        }
+        if (usable(a, ok, g, stage) && (pk[g] >> 16) == 1) claim_and_bid(g, 0);
     __syncthreads();
-    int nf = s_nf0;
 
     LevelCursor cur;
     for (;;) {
         const int par = cur.level & 1;
-        // A: frontier constraints bid for their single unknown
-        for (int i = tid; i < nf; i += T) {
-            const int32_t g = front[i];
-            const uint32_t w = pk[g];
-            if (((w >> 16) & 0x7fffu) != 1) continue;  // its unknown was decoded by another constraint
-            const int32_t f = (int32_t)(w & 0xffffu);
-            const uint32_t key = ((uint32_t)deg[g] << 16) | (uint32_t)g;
-            if (atomicMin(best + f, key) == kE) touched[append_slot(&s_nt[par])] = (uint16_t)f;
-        }
-        __syncthreads();
         const int nt = s_nt[par];
+        const uint16_t *touched = touched2 + (size_t)par * (K + 1);
         if (nt == 0) {
             if (stage != 0) break;
             // two-pass: the coded rows reached their fixpoint; peel the checks
             stage = 1;
-            if (tid == 0) s_nf0 = 0;
-            __syncthreads();
+            __syncthreads();  // every thread has read the empty count
             for (int32_t g = a.n + tid; g < G; g += T)
-                if (((pk[g] >> 16) & 0x7fffu) == 1) {
-                    pk[g] |= kClaim;
-                    front[append_slot(&s_nf0)] = (uint16_t)g;
-                }
+                if (((pk[g] >> 16) & 0x7fffu) == 1) claim_and_bid(g, par);
             __syncthreads();
-            nf = s_nf0;
             continue;
         }
         // B: pairs of the level (adjacency slots into lvl_v for step C)
-        const int4 len = emit_level(
+        emit_level(
             a, cur, nt,
             [&](int i, int32_t *f, int32_t *g, int32_t *vdeg) {
                 *f = touched[i];
                 *g = (int32_t)(best[*f] & 0xffffu);
                 *vdeg = vptr[*f + 1] - vptr[*f];
             },
-            cptr4, lvl_v, s_warp4);
-        const bool mapped = len.w <= kSlotCap;  // uniform: slots of each pair listed
+            cptr4, lvl_v, s_warp4, &s_len);
         for (int i = tid; i < nt; i += T) {
             const int32_t f = touched[i];
             best[f] = kE;
             known[f] = 1;
-            if (mapped)
+        }
+        if (tid == 0) s_nt[par ^ 1] = 0;  // the list the next level's bids fill
+        __syncthreads();
+        const int4 len = s_len;
+        const bool mapped = len.w <= kSlotCap;  // uniform: slots of each pair listed
+        if (mapped) {
+            for (int i = tid; i < nt; i += T) {
+                const int32_t f = touched[i];
                 for (int32_t u = lvl_v[i], u1 = lvl_v[i] + vptr[f + 1] - vptr[f]; u < u1; ++u)
                     slots[u] = (uint16_t)i;
+            }
+            __syncthreads();
         }
-        if (tid == 0) {  // the counters the next level appends to (read by now)
-            s_nt[par ^ 1] = 0;
-            s_nnext[par ^ 1] = 0;
-        }
-        __syncthreads();
         // C1: one thread per adjacency slot: res -= 1 and xs ^= f on one
         // constraint containing a newly decoded symbol, without waiting for
         // a result; the slot's constraint is remembered for C2
@@ -545,8 +557,8 @@ __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCo
             if (mapped) slots[u] = (uint16_t)c;
         }
         __syncthreads();
-        // C2: a touched constraint left with one unknown joins the next
-        // frontier once (its claim bit is set by the one thread that appends)
+        // C2 (and step A of the next level): a touched constraint left with
+        // one unknown claims itself once and bids for that unknown
         for (int32_t u = tid; u < len.w; u += T) {
             int32_t c;
             if (mapped) {
@@ -557,16 +569,11 @@ __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCo
                 c = vidx[vptr[f] + (u - lvl_v[i])];
             }
             const uint32_t w = pk[c];
-            if ((w & kClaim) == 0 && (w >> 16) == 1 && usable(a, ok, c, stage) &&
-                (atomicOr(pk + c, kClaim) & kClaim) == 0)
-                next[append_slot(&s_nnext[par])] = (uint16_t)c;
+            if ((w & kClaim) == 0 && (w >> 16) == 1 && usable(a, ok, c, stage))
+                claim_and_bid(c, par ^ 1);
         }
         __syncthreads();
-        nf = s_nnext[par];
         advance(cur, nt, len);
-        uint16_t *tmp = front;
-        front = next;
-        next = tmp;
     }
     finish_dpg(a, cur, known, &s_cnt, &s_cnt_data);
 }
@@ -590,9 +597,8 @@ DpgCompactPlace plan_dpg_compact(const fs_code *c) {
     p.cptr4 = take(4 * (G + 1));
     p.vptr = take(4 * (K + 1));
     p.lvl_v = take(4 * (K + 1));
-    p.front = take(2 * (G + 1));
-    p.next = take(2 * (G + 1));
-    p.touched = take(2 * (K + 1));
+    p.front = take(2 * 2 * (K + 1));  // the two symbol lists
+    p.next = p.touched = -1;
     p.deg = take(2 * (G + 1));
     p.slots = take(2 * (int64_t)kSlotCap);
     p.vidx = take(2 * (c->e_con + 1));
@@ -610,7 +616,7 @@ struct PeelArgs {
     const uint4 *coded;
     uint4 *data;    // intermediates v < b
     uint4 *parity;  // intermediates v >= b (workspace)
-    const int32_t *con_idx4, *seg_pair, *unrec_list, *hdr;
+    const int32_t *con_idx4, *seg_pair, *chunk_pair, *unrec_list, *hdr;
     const int4 *pair_rec, *level_tab;
     int32_t b, n;
     int64_t tw;
@@ -683,7 +689,7 @@ __device__ __forceinline__ void xor_shared(uint4 *d, const uint4 &v) {
 __device__ void peel_direct(const PeelArgs &a, int64_t w0, int lanes) {
     const int32_t n_levels = a.hdr[WS_N_LEVELS];
     for (int32_t l = 0; l < n_levels; ++l) {
-        const int4 lt = a.level_tab[l];
+        const int4 lt = a.level_tab[2 * l];
         const int32_t items = lt.y * lanes;
         for (int32_t it = threadIdx.x; it < items; it += blockDim.x) {
             const int32_t q = it / lanes, lane = it - q * lanes;
@@ -703,18 +709,20 @@ __device__ void peel_direct(const PeelArgs &a, int64_t w0, int lanes) {
     }
 }
 
-// Warp 0: bulk copies of level l's pair records and segment list into slot.
+// One thread: bulk copies of level l's pair records, segment list and chunk
+// list into their slots (one mbarrier phase).
 __device__ __forceinline__ void issue_pairs(const PeelArgs &a, const int4 *ltab, int l,
                                             int32_t *pairs_slot, int32_t *segs_slot,
-                                            uint64_t *bar) {
-    if ((threadIdx.x & 31) != 0) return;
-    const int4 lt = ltab[l];
+                                            int32_t *chunks_slot, uint64_t *bar) {
+    const int4 lt = ltab[2 * l], lc = ltab[2 * l + 1];
     const uint32_t pb = (uint32_t)lt.y * kRec * 4;
     const uint32_t sbytes = (uint32_t)((lt.w + 3) & ~3) * 4;
+    const uint32_t cbytes = (uint32_t)((lc.y + 3) & ~3) * 4;
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    mbar_expect_tx(bar, pb + sbytes);
+    mbar_expect_tx(bar, pb + sbytes + cbytes);
     bulk_g2s(pairs_slot, a.pair_rec + 2 * (size_t)lt.x, pb, bar);
     if (sbytes) bulk_g2s(segs_slot, a.seg_pair + lt.z, sbytes, bar);
+    if (cbytes) bulk_g2s(chunks_slot, a.chunk_pair + lc.x, cbytes, bar);
 }
 
 __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
@@ -723,22 +731,14 @@ __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
 }
 
 // All threads: level l's recipes (its padded graph rows, 16 bytes per copy)
-// into rows_slot from its staged pair records, and an L2 prefetch of its
-// coded payload slices.
+// into rows_slot from its staged pair records and chunk list, and an L2
+// prefetch of its coded payload slices.
 __device__ __forceinline__ void stage_rows(const PeelArgs &a, const int4 *ltab, int l,
-                                           const int32_t *prec, int32_t *rows_slot, int64_t w0,
-                                           int lanes) {
-    const int np = ltab[l].y;
-    const int32_t *last = prec + (size_t)(np - 1) * kRec;
-    const int n16 = (last[2] + last[5]) >> 2;
-    for (int c = threadIdx.x; c < n16; c += blockDim.x) {
-        int lo = 0, hi = np - 1;  // pair whose row holds entry 4c
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (prec[(size_t)mid * kRec + 2] <= 4 * c) lo = mid;
-            else hi = mid - 1;
-        }
-        const int32_t *r = prec + (size_t)lo * kRec;
+                                           const int32_t *prec, const int32_t *chunks,
+                                           int32_t *rows_slot, int64_t w0, int lanes) {
+    const int np = ltab[2 * l].y, nc = ltab[2 * l + 1].y;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const int32_t *r = prec + (size_t)chunks[c] * kRec;
         cp_async16(rows_slot + 4 * c, a.con_idx4 + r[4] + (4 * c - r[2]));
     }
     const int lines = (lanes * 16 + 127) >> 7;
@@ -773,12 +773,13 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
     if (!a.hdr[WS_STAGED]) {
         peel_direct(a, w0, lanes);
     } else {
-        int4 *ltab = reinterpret_cast<int4 *>(smem);                            // [levels + 1]
-        int32_t *pairs = reinterpret_cast<int32_t *>(ltab + kStageLevels + 1);  // [3][P * kRec]
-        int32_t *segs = pairs + 3 * kStagePairs * kRec;                         // [3][S]
-        int32_t *rows = segs + 3 * kStageSegs;                                  // [2][R]
+        int4 *ltab = reinterpret_cast<int4 *>(smem);                  // [2 (levels + 1)]
+        int32_t *pairs = reinterpret_cast<int32_t *>(ltab + 2 * (kStageLevels + 1));  // [3][P*kRec]
+        int32_t *segs = pairs + 3 * kStagePairs * kRec;                // [3][S]
+        int32_t *chunks = segs + 3 * kStageSegs;                       // [3][R / 4]
+        int32_t *rows = chunks + 3 * (kStageRecipe / 4);               // [2][R]
         uint4 *accs = reinterpret_cast<uint4 *>(rows + 2 * kStageRecipe);  // [kStageMulti][L]
-        for (int i = threadIdx.x; i <= nl; i += blockDim.x) ltab[i] = a.level_tab[i];
+        for (int i = threadIdx.x; i < 2 * (nl + 1); i += blockDim.x) ltab[i] = a.level_tab[i];
         for (int i = threadIdx.x; i < kStageMulti * L; i += blockDim.x)
             accs[i] = make_uint4(0, 0, 0, 0);
         if (threadIdx.x == 0) {
@@ -791,11 +792,11 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
         if (threadIdx.x == 0) {
             for (int l = 0; l < 2 && l < nl; ++l)
                 issue_pairs(a, ltab, l, pairs + l * kStagePairs * kRec, segs + l * kStageSegs,
-                            &mb_pairs[l]);
+                            chunks + l * (kStageRecipe / 4), &mb_pairs[l]);
             s_ok = (nl == 0 || mbar_wait(&mb_pairs[0], 0)) ? 1 : 0;
         }
         __syncthreads();
-        if (s_ok && nl > 0) stage_rows(a, ltab, 0, pairs, rows, w0, lanes);
+        if (s_ok && nl > 0) stage_rows(a, ltab, 0, pairs, chunks, rows, w0, lanes);
         cp_async_commit();
         for (int32_t l = 0; l < nl; ++l) {
             const int ps = l % 3, rslot = l & 1;
@@ -817,12 +818,14 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             // rows of l+1 (every thread)
             if (threadIdx.x == 0 && l + 2 < nl)
                 issue_pairs(a, ltab, l + 2, pairs + ((l + 2) % 3) * kStagePairs * kRec,
-                            segs + ((l + 2) % 3) * kStageSegs, &mb_pairs[(l + 2) % 3]);
+                            segs + ((l + 2) % 3) * kStageSegs,
+                            chunks + ((l + 2) % 3) * (kStageRecipe / 4), &mb_pairs[(l + 2) % 3]);
             if (l + 1 < nl)
                 stage_rows(a, ltab, l + 1, pairs + ((l + 1) % 3) * kStagePairs * kRec,
+                           chunks + ((l + 1) % 3) * (kStageRecipe / 4),
                            rows + ((l + 1) & 1) * kStageRecipe, w0, lanes);
             cp_async_commit();
-            const int4 lt = ltab[l];
+            const int4 lt = ltab[2 * l];
             const int np = lt.y, ns = lt.w;
             // every (segment, word pair): one gather of at most kRecipeSeg blocks
             for (int it = threadIdx.x; it < ns * nv; it += blockDim.x) {
@@ -890,8 +893,9 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
 }
 
 size_t peel_smem_bytes(int64_t L) {
-    return (size_t)(kStageLevels + 1) * 16 + (size_t)3 * kStagePairs * kRec * 4 +
-           (size_t)3 * kStageSegs * 4 + (size_t)2 * kStageRecipe * 4 +
+    return (size_t)(kStageLevels + 1) * 32 + (size_t)3 * kStagePairs * kRec * 4 +
+           (size_t)3 * kStageSegs * 4 + (size_t)3 * (kStageRecipe / 4) * 4 +
+           (size_t)2 * kStageRecipe * 4 +
            (size_t)kStageMulti * L * 16;
 }
 
@@ -925,6 +929,7 @@ cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws, uin
     a.level_off = reinterpret_cast<int32_t *>(ws + L.level_off);
     a.level_tab = reinterpret_cast<int4 *>(ws + L.level_tab);
     a.seg_pair = reinterpret_cast<int32_t *>(ws + L.seg_pair);
+    a.chunk_pair = reinterpret_cast<int32_t *>(ws + L.chunk_pair);
     a.unrec_list = reinterpret_cast<int32_t *>(ws + L.unrec_list);
     a.hdr = reinterpret_cast<int32_t *>(ws);
     a.unrecovered = unrecovered;
@@ -958,6 +963,7 @@ cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, u
     a.parity = reinterpret_cast<uint4 *>(ws + L.parity);
     a.con_idx4 = c->con_idx4;
     a.seg_pair = reinterpret_cast<const int32_t *>(ws + L.seg_pair);
+    a.chunk_pair = reinterpret_cast<const int32_t *>(ws + L.chunk_pair);
     a.unrec_list = reinterpret_cast<const int32_t *>(ws + L.unrec_list);
     a.hdr = reinterpret_cast<const int32_t *>(ws);
     a.pair_rec = reinterpret_cast<const int4 *>(ws + L.pair_rec);

@@ -52,14 +52,10 @@ def test_static_encode_matches_encode_twice_in_a_row():
                 assert np.array_equal(p1.cpu().numpy(), p0.cpu().numpy())
 
 
-def test_static_encode_rejects_codes_beyond_its_area():
-    """A code whose encode needs more scratch than the static area is refused
-    on the host, before any device work."""
+def test_static_encode_area_covers_large_blocks():
+    """The static area holds the encode workspace of large-block codes too:
+    the host check that would refuse a code beyond it lets them through."""
     from paper_1702_07409_gb300 import founsure as fs
     g = gen.make_graph(8, 0, 12, gen.DIST_RSD, 0.1, 0.05)
-    t = 256 * 1024 * 1024  # 256 MiB blocks: more byte chunks than the area counts
-    code = fs.Code(g, t)
-    assert code.workspace_bytes(fs.OP_ENCODE) > fs.ENCODE_STATIC_SCRATCH_BYTES
-    fake = ctypes.c_void_p(1 << 20)  # aligned, never dereferenced: the call is refused first
-    rc = fs.lib().fs_encode_static(code._h, fake, None, fake, None, None)
-    assert rc == fs.FS_ERR_SCRATCH
+    code = fs.Code(g, 256 * 1024 * 1024)  # 256 MiB blocks; nothing is allocated for them
+    assert code.workspace_bytes(fs.OP_ENCODE) <= fs.ENCODE_STATIC_SCRATCH_BYTES
