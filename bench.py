@@ -252,6 +252,8 @@ def run_gpu(args):
         tuning[fs.TUNE_PEEL_CTAS] = args.peel_ctas
     if args.gather_ctas:
         tuning[fs.TUNE_GATHER_CTAS] = args.gather_ctas
+    if args.l2_hints:
+        tuning[fs.TUNE_L2_HINTS] = 1
 
     st = Stripe(rank, max(args.steps, 1) + args.warmup, device, tuning,
                 overlap=not args.serial_schedule)
@@ -442,6 +444,8 @@ def main():
     ap.add_argument("--cpu-slice", type=int, default=16384,
                     help="bytes of each block the CPU oracle processes per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--l2-hints", action="store_true",
+                    help="tuning knob: L2 evict-last / evict-first hints")
     ap.add_argument("--serial-schedule", action="store_true",
                     help="run the decoding schedule after the encode instead of beside it")
     ap.add_argument("--peel-ctas", type=int, default=0, help="tuning knob (1..8)")

@@ -111,11 +111,24 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
  *                        indices and the whole graph in shared memory when
  *                        the code has at most 65536 intermediates and
  *                        constraints; 0: the general form
+ *   FS_TUNE_L2_HINTS     1: encode and payload peel mark the blocks they
+ *                        gather again as evict-last in L2 and streamed data
+ *                        as evict-first; 0 (default): plain loads and stores
+ *   FS_TUNE_ENCODE_SLICES 1 (default): encode holds one byte slice of every
+ *                        data block and parity in shared memory and computes
+ *                        all rows of that slice from it, when the code fits
+ *                        (about 7000 data blocks + parities): 32-byte
+ *                        slices when two buffers of them fit in shared
+ *                        memory, else 16-byte slices; 2: always 16-byte
+ *                        slices; 3: always 32-byte slices (when they fit);
+ *                        0: row-gather encode through L2
  * Returns FS_ERR_INVALID for an unknown knob or an out-of-range value. Not
  * thread-safe against concurrent hot calls on the same code. */
 #define FS_TUNE_PEEL_CTAS   1
 #define FS_TUNE_GATHER_CTAS 2
 #define FS_TUNE_DPG_COMPACT 3
+#define FS_TUNE_L2_HINTS    4
+#define FS_TUNE_ENCODE_SLICES 5
 fs_status fs_code_set_tuning(fs_code *code, int knob, int value);
 
 /* Bytes of caller-provided device workspace that op needs. n_items is the

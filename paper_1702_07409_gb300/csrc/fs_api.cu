@@ -54,6 +54,7 @@ void free_code(fs_code *c) {
     cudaFree(c->var_idx);
     cudaFree(c->con_ptr4);
     cudaFree(c->con_idx4);
+    free_slice_tables(c);
     free(c);
 }
 
@@ -161,6 +162,8 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     c->peel_ctas = 1;
     c->gather_ctas = 8;
     c->dpg_compact = 1;
+    c->l2_hints = 0;
+    c->encode_slices = 1;
     cudaError_t e = cudaGetDevice(&c->device);
     int v = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c->device);
@@ -177,6 +180,7 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     if (e == cudaSuccess) e = upload(&c->var_idx, var_idx);
     if (e == cudaSuccess) e = upload(&c->con_ptr4, con_ptr4);
     if (e == cudaSuccess) e = upload(&c->con_idx4, con_idx4);
+    if (e == cudaSuccess) e = build_slice_tables(c, con_ptr.data(), con_idx.data());
     if (e != cudaSuccess) {
         free_code(c);
         return e == cudaErrorMemoryAllocation ? FS_ERR_NOMEM : FS_ERR_CUDA;
@@ -211,6 +215,14 @@ FS_API fs_status fs_code_set_tuning(fs_code *c, int knob, int value) {
         case FS_TUNE_DPG_COMPACT:
             if (value != 0 && value != 1) return FS_ERR_INVALID;
             c->dpg_compact = value;
+            return FS_OK;
+        case FS_TUNE_ENCODE_SLICES:
+            if (value < 0 || value > 3) return FS_ERR_INVALID;
+            c->encode_slices = value;
+            return FS_OK;
+        case FS_TUNE_L2_HINTS:
+            if (value != 0 && value != 1) return FS_ERR_INVALID;
+            c->l2_hints = value;
             return FS_OK;
         case FS_TUNE_GATHER_CTAS:
             if (value < 1 || value > 16) return FS_ERR_INVALID;

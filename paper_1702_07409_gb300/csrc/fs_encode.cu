@@ -1,8 +1,21 @@
-// fs_encode.cu - encoding (Section 2.2, steps (1) precode and (2) LDGM) in
-// two launches of one kernel, k_rows: first the m precode rows (parities,
-// over the data blocks), then the n LT rows (coded blocks, over the data
-// blocks and parities). Stream order makes every parity final before an LT
-// row reads it.
+// fs_encode.cu - encoding (Section 2.2, steps (1) precode and (2) LDGM).
+//
+// k_slices (the default when the code fits): one persistent CTA per SM takes
+// 16-byte byte slices of the stripe from a ticket counter. For a slice it
+// loads that slice of every data block into shared memory with 2-D TMA
+// copies (a box is 16 bytes x up to 256 blocks), computes the m parity
+// slices there (one warp per precode row, lanes splitting the row, a shuffle
+// reduction), then the n coded slices (one lane per coded row; rows sorted
+// by degree into warp groups so the lanes of a warp do equal work, their
+// slot lists column-major so a warp reads its indices in one transaction).
+// Every gathered operand comes from shared memory: each input byte crosses
+// DRAM once and L2 only serves the index tables. Two slice buffers let the
+// TMA copies of the next slice run under the arithmetic of the current one.
+//
+// k_rows (fallback for codes whose slice does not fit) in two launches:
+// first the m precode rows (parities, over the data blocks), then the n LT
+// rows (coded blocks, over the data blocks and parities). Stream order makes
+// every parity final before an LT row reads it.
 //
 // Work is taken in tickets (byte chunk, batch of consecutive rows: one check
 // row for the precode, kRows coded rows for LT),
@@ -16,16 +29,25 @@
 // neighbours x kEncV words of loads in flight whatever the row degrees, and
 // a finished row is stored as soon as the walk passes its end. Coded rows
 // are written with evict-first stores so L2 keeps the inputs.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
 #include "fs_internal.cuh"
 
 namespace {
 
 constexpr int kEncThreads = 256;
-constexpr int kEncV = 2;                      // words per thread per chunk
-constexpr int kChunkW = kEncV * kEncThreads;  // 16-byte words per chunk (8 KiB)
+constexpr int kEncV = 1;                      // words per thread per chunk
+constexpr int kChunkW = kEncV * kEncThreads;  // 16-byte words per chunk (4 KiB)
 constexpr int kRows = 16;                     // rows per ticket
 constexpr int kStage = 2048;                  // neighbour entries of one ticket staged
-constexpr int kCtasPerSm = 3;
+constexpr int kCtasPerSm = 5;
 
 struct RowArgs {
     const int32_t *ptr, *idx;  // CSR rows
@@ -37,6 +59,7 @@ struct RowArgs {
     int32_t n_chunks;
     int stream_out;       // 1: evict-first stores
     int32_t rows;         // rows per ticket (at most kRows)
+    int hints;            // 1: inputs evict-last, outputs evict-first in L2
     int32_t *ticket_ctr;  // workspace counter, zero at launch
 };
 
@@ -75,13 +98,14 @@ __device__ __forceinline__ Ticket ticket_of(const RowArgs &a, int32_t t, int32_t
 }
 
 __device__ __forceinline__ void store_row(const RowArgs &a, int32_t row, int64_t w0, int64_t w1,
-                                          const uint4 *acc) {
+                                          const uint4 *acc, uint64_t pol_out) {
     uint4 *out = a.out + (int64_t)row * a.tw;
 #pragma unroll
     for (int v = 0; v < kEncV; ++v) {
         const int64_t w = w0 + threadIdx.x + (int64_t)v * kEncThreads;
         if (w >= w1) continue;
-        if (a.stream_out) __stcs(out + w, acc[v]);
+        if (a.hints) st_hint(out + w, acc[v], pol_out);
+        else if (a.stream_out) __stcs(out + w, acc[v]);
         else __stcg(out + w, acc[v]);
     }
 }
@@ -146,6 +170,8 @@ __global__ void __launch_bounds__(kEncThreads, kCtasPerSm) k_rows(RowArgs a) {
             ok[v] = w[v] < w1;
             acc[v] = make_uint4(0, 0, 0, 0);
         }
+        const uint64_t pol_in = l2_policy_last();
+        const uint64_t pol_out = a.stream_out ? l2_policy_first() : l2_policy_last();
         int r = 0;  // row being accumulated; entries [rp[r], rp[r + 1])
         for (int32_t e = e_base; e < e_end; e += 8) {
             uint4 x[8][kEncV];
@@ -157,13 +183,15 @@ __global__ void __launch_bounds__(kEncThreads, kCtasPerSm) k_rows(RowArgs a) {
                                                : a.inB + (int64_t)(v - a.split) * a.tw;
 #pragma unroll
                 for (int q = 0; q < kEncV; ++q)
-                    x[j][q] = (on && ok[q]) ? __ldg(src + w[q]) : make_uint4(0, 0, 0, 0);
+                    x[j][q] = (on && ok[q]) ? (a.hints ? ld_nc_hint(src + w[q], pol_in)
+                                                       : __ldg(src + w[q]))
+                                            : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 if (e + j >= e_end) break;
                 while (e + j >= rp[r + 1]) {  // row r is complete (rows may be empty)
-                    store_row(a, k.r0 + r, w0, w1, acc);
+                    store_row(a, k.r0 + r, w0, w1, acc, pol_out);
 #pragma unroll
                     for (int v = 0; v < kEncV; ++v) acc[v] = make_uint4(0, 0, 0, 0);
                     ++r;
@@ -173,12 +201,267 @@ __global__ void __launch_bounds__(kEncThreads, kCtasPerSm) k_rows(RowArgs a) {
             }
         }
         for (; r < k.nr; ++r) {  // the last row with entries, then empty rows
-            store_row(a, k.r0 + r, w0, w1, acc);
+            store_row(a, k.r0 + r, w0, w1, acc, pol_out);
 #pragma unroll
             for (int v = 0; v < kEncV; ++v) acc[v] = make_uint4(0, 0, 0, 0);
         }
     }
     cp_async_wait<0>();
+}
+
+// ---- shared-memory slice encode --------------------------------------------
+
+constexpr int kSliceThreads = 1024;
+constexpr long long kSliceWait = 1ll << 22;  // bounded mbarrier waits
+constexpr uint16_t kNoSlot = 0xFFFF;
+
+struct SliceArgs {
+    const uint4 *tab;         // tables (copied to shared memory at start)
+    int32_t tab_words;        // 16-byte words of tab
+    int32_t off_row, off_pptr, off_pre, off_idx;  // byte offsets inside tab
+    uint4 *parity, *coded;
+    int32_t m, n_grp, bpad, zbase, slots, box_rows, n_boxes, nbuf;
+    int64_t tw;               // 16-byte words per block
+    int32_t n_slices;         // byte slices of the stripe
+    int32_t *ticket;          // workspace counter, zero at launch
+    int32_t *status;
+};
+
+__device__ __forceinline__ uint32_t saddr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void xor_in(uint4 &a, const uint4 &b) {
+    a.x ^= b.x;
+    a.y ^= b.y;
+    a.z ^= b.z;
+    a.w ^= b.w;
+}
+
+// 16-byte word h of slot s. With 32-byte slots the TMA copies use the 32B
+// swizzle (address bit 4 ^= bit 7), so the halves of slot s trade places
+// when bit 2 of s is set; either way the 8 slots s with distinct s & 7 lie
+// in 8 distinct bank groups for a fixed h.
+template <int V>
+__device__ __forceinline__ int32_t unit_of(int32_t s, int h) {
+    return V == 1 ? s : 2 * s + (h ^ ((s >> 2) & 1));
+}
+
+// Issues the TMA copies of slice `tk` (all data blocks) into `buf`.
+template <int V>
+__device__ __forceinline__ void issue_slice(const CUtensorMap *map, const SliceArgs &a, int32_t tk,
+                                            uint4 *buf, uint64_t *bar) {
+    const uint32_t bytes = (uint32_t)a.n_boxes * (uint32_t)a.box_rows * 16u * V;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(bar)),
+                 "r"(bytes)
+                 : "memory");
+    const int32_t x = tk * 16 * V;  // byte offset of the slice inside a block
+    for (int i = 0; i < a.n_boxes; ++i) {
+        const int32_t y = i * a.box_rows;
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(saddr(buf + (size_t)y * V)),
+            "l"(map), "r"(x), "r"(y), "r"(saddr(bar))
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity) {
+    const uint32_t addr = saddr(bar);
+    for (long long i = 0; i < kSliceWait; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Views of the tables once they sit in shared memory.
+struct SliceTables {
+    const int2 *grp;
+    const uint16_t *grow, *pre, *gidx;
+    const int32_t *pptr;
+};
+
+template <int V>
+__device__ __forceinline__ void gather(uint4 *acc, const uint4 *slot, uint16_t s) {
+#pragma unroll
+    for (int h = 0; h < V; ++h) xor_in(acc[h], slot[unit_of<V>(s, h)]);
+}
+
+// Parity and coded slices of byte slice t from the data slots of `slot`
+// (parity j goes to slot bpad + j). Ends with a barrier.
+template <int V>
+__device__ __forceinline__ void compute_slice(const SliceArgs &a, const SliceTables &tb, uint4 *slot,
+                                              int32_t t) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t w0 = (int64_t)t * V;  // first 16-byte word of the slice
+    // step (1): parity slices, one quarter warp (8 lanes) per precode row;
+    // a row's member list is whole octets, each in 8 distinct bank groups
+    const int quarter = lane >> 3, p8 = lane & 7;
+    for (int task = warp; task * 4 < a.m; task += nw) {
+        const int j = task * 4 + quarter;
+        const bool on = j < a.m;
+        const int32_t e0 = on ? tb.pptr[j] : 0;
+        const int n_oct = on ? (tb.pptr[j + 1] - e0) >> 3 : 0;
+        const int n_max = __reduce_max_sync(0xffffffffu, n_oct);
+        uint4 acc[V];
+#pragma unroll
+        for (int h = 0; h < V; ++h) acc[h] = make_uint4(0, 0, 0, 0);
+        const uint16_t zs = (uint16_t)(a.zbase + p8);  // a zero slot in this lane's own group
+        int k = 0;
+        for (; k + 2 <= n_max; k += 2) {
+            const uint16_t s0 = k < n_oct ? tb.pre[e0 + 8 * k + p8] : zs;
+            const uint16_t s1 = k + 1 < n_oct ? tb.pre[e0 + 8 * k + 8 + p8] : zs;
+            gather<V>(acc, slot, s0);
+            gather<V>(acc, slot, s1);
+        }
+        if (k < n_max) gather<V>(acc, slot, k < n_oct ? tb.pre[e0 + 8 * k + p8] : zs);
+#pragma unroll
+        for (int h = 0; h < V; ++h) {
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                acc[h].x ^= __shfl_xor_sync(0xffffffffu, acc[h].x, o);
+                acc[h].y ^= __shfl_xor_sync(0xffffffffu, acc[h].y, o);
+                acc[h].z ^= __shfl_xor_sync(0xffffffffu, acc[h].z, o);
+                acc[h].w ^= __shfl_xor_sync(0xffffffffu, acc[h].w, o);
+            }
+        }
+        if (on && p8 == 0) {
+#pragma unroll
+            for (int h = 0; h < V; ++h) {
+                slot[unit_of<V>(a.bpad + j, h)] = acc[h];
+                if (w0 + h < a.tw) a.parity[(int64_t)j * a.tw + w0 + h] = acc[h];
+            }
+        }
+    }
+    __syncthreads();
+    // step (2): coded slices, one lane per coded row, warp groups of 4 quarters
+    for (int q = warp; q < a.n_grp; q += nw) {
+        const int2 gq = tb.grp[q];
+        const uint16_t *ix = tb.gidx + gq.x + lane;
+        uint4 acc[V];
+#pragma unroll
+        for (int h = 0; h < V; ++h) acc[h] = make_uint4(0, 0, 0, 0);
+        // padding cells name a zero slot in a bank group the column leaves free
+        int j = 0;
+        for (; j + 4 <= gq.y; j += 4) {
+            uint16_t s4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s4[u] = ix[(j + u) * 32];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) gather<V>(acc, slot, s4[u]);
+        }
+        for (; j < gq.y; ++j) gather<V>(acc, slot, ix[j * 32]);
+        const uint16_t row = tb.grow[q * 32 + lane];
+        if (row != kNoSlot) {
+#pragma unroll
+            for (int h = 0; h < V; ++h)
+                if (w0 + h < a.tw) __stcs(a.coded + (int64_t)row * a.tw + w0 + h, acc[h]);
+        }
+    }
+    __syncthreads();  // the slots are free again
+}
+
+// V 16-byte words per slot (slices of 16 V bytes), data slices by 2-D TMA
+// boxes (one thread issues, an mbarrier completes), nbuf slot buffers.
+template <int V>
+__global__ void __launch_bounds__(kSliceThreads, 1)
+    k_slices(const __grid_constant__ CUtensorMap map, SliceArgs a) {
+    extern __shared__ __align__(1024) unsigned char s_raw[];
+    // offset from s_raw (not integer casts) so every access stays a shared-space load
+    uint4 *slot0 = reinterpret_cast<uint4 *>(s_raw + ((1024u - (saddr(s_raw) & 1023u)) & 1023u));
+    const size_t buf_words = (size_t)a.slots * V;
+    uint4 *s_tab = slot0 + (size_t)a.nbuf * buf_words;
+    const unsigned char *tp = reinterpret_cast<const unsigned char *>(s_tab);
+    SliceTables tb;
+    tb.grp = reinterpret_cast<const int2 *>(tp);
+    tb.grow = reinterpret_cast<const uint16_t *>(tp + a.off_row);
+    tb.pptr = reinterpret_cast<const int32_t *>(tp + a.off_pptr);
+    tb.pre = reinterpret_cast<const uint16_t *>(tp + a.off_pre);
+    tb.gidx = reinterpret_cast<const uint16_t *>(tp + a.off_idx);
+    __shared__ uint64_t s_bar[2];
+    __shared__ int32_t s_tk[2];
+    __shared__ int32_t s_ok;
+    const int32_t n_slices = a.n_slices;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&s_bar[i])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        s_tk[0] = atomicAdd(a.ticket, 1);
+        if (s_tk[0] < n_slices) issue_slice<V>(&map, a, s_tk[0], slot0, &s_bar[0]);
+    }
+    // the tables, once per CTA, under the first slice's copies; the zero slots
+    for (int32_t i = threadIdx.x; i < a.tab_words; i += blockDim.x) s_tab[i] = __ldg(a.tab + i);
+    for (int i = threadIdx.x; i < 2 * 8 * V; i += blockDim.x) {
+        const int bb = i / (8 * V), r = i % (8 * V);
+        if (bb < a.nbuf) slot0[(size_t)bb * buf_words + (size_t)a.zbase * V + r] = make_uint4(0, 0, 0, 0);
+    }
+
+    uint32_t uses0 = 0, uses1 = 0;  // completed phases of each buffer's barrier
+    for (int it = 0;; ++it) {
+        const int b = a.nbuf == 2 ? (it & 1) : 0;
+        uint4 *slot = slot0 + (size_t)b * buf_words;
+        if (threadIdx.x == 0) {
+            if (a.nbuf == 2) {  // next slice into the other buffer (free since the last barrier)
+                const int32_t nx = atomicAdd(a.ticket, 1);
+                s_tk[(it + 1) & 1] = nx;
+                if (nx < n_slices)
+                    issue_slice<V>(&map, a, nx, slot0 + (size_t)(b ^ 1) * buf_words, &s_bar[b ^ 1]);
+            }
+            const int32_t t = s_tk[it & 1];
+            int ok = 1;
+            if (t < n_slices) {
+                ok = wait_phase(&s_bar[b], (b ? uses1 : uses0) & 1) ? 1 : 0;
+                if (!ok) {
+                    atomicExch(a.status, (int32_t)FS_ERR_TIMEOUT);
+                    // give the other buffer's copies (if any) a bounded time to land
+                    if (a.nbuf == 2 && s_tk[(it + 1) & 1] < n_slices)
+                        wait_phase(&s_bar[b ^ 1], (b ? uses0 : uses1) & 1);
+                }
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        const int32_t t = s_tk[it & 1];
+        if (t >= n_slices || !s_ok) break;
+        if (b) ++uses1;
+        else ++uses0;
+        compute_slice<V>(a, tb, slot, t);
+        if (a.nbuf == 1 && threadIdx.x == 0) {
+            const int32_t nx = atomicAdd(a.ticket, 1);
+            s_tk[(it + 1) & 1] = nx;
+            if (nx < n_slices) issue_slice<V>(&map, a, nx, slot0, &s_bar[0]);
+        }
+    }
+}
+
+using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeTiledFn tensor_map_encoder() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+size_t slice_smem_bytes(const fs_code *c, int v, int nbuf) {
+    // slot buffers, tables, alignment slack
+    return (size_t)nbuf * (size_t)c->sl_slots * 16 * v + (size_t)c->sl_tab_bytes + 1024;
 }
 
 int grid_for(int64_t n_tiles, int num_sms, int ctas_per_sm) {
@@ -196,17 +479,331 @@ int32_t encode_chunks(const fs_code *c) {
 // status word + one ticket counter per launch (header words WS_COUNT_A/B)
 size_t encode_ws_bytes(const fs_code *) { return WS_HDR_BYTES; }
 
+namespace {
+
+// Shared memory serves a warp's 16-byte loads a quarter-warp (8 lanes) at a
+// time, and slot s lies in bank group s & 7: 8 lanes that read 8 different
+// groups take one pass, two lanes in the same group take two. The tables
+// below order the work so that every quarter-warp reads distinct groups.
+inline int bank_group(uint16_t slot) { return slot & 7; }
+
+// Colours the edges of a bipartite multigraph (8 rows x 8 bank groups) with
+// delta colours, no two edges of one colour sharing an end (Koenig's theorem;
+// a clash is cleared by swapping the two colours along an alternating path).
+// edges: (row position, group); returns the colour of each edge.
+std::vector<int> colour_edges(const std::vector<std::pair<int, int>> &edges, int delta) {
+    std::vector<int> at_r(8 * (size_t)delta, -1), at_g(8 * (size_t)delta, -1);
+    std::vector<int> col(edges.size(), -1);
+    std::vector<int> path;
+    for (size_t e = 0; e < edges.size(); ++e) {
+        const int r = edges[e].first, g = edges[e].second;
+        int a = 0, b = 0;
+        while (at_r[r * delta + a] >= 0) ++a;  // free at the row
+        while (at_g[g * delta + b] >= 0) ++b;  // free at the group
+        if (at_g[g * delta + a] >= 0) {
+            // path from g along colours a, b, a, ...; it cannot reach r (a is free there)
+            path.clear();
+            int v = g, x = a, y = b;
+            bool at_group = true;
+            for (;;) {
+                const int f = at_group ? at_g[v * delta + x] : at_r[v * delta + x];
+                if (f < 0) break;
+                path.push_back(f);
+                v = at_group ? edges[f].first : edges[f].second;
+                at_group = !at_group;
+                std::swap(x, y);
+            }
+            for (int f : path) {
+                at_r[edges[f].first * delta + col[f]] = -1;
+                at_g[edges[f].second * delta + col[f]] = -1;
+            }
+            for (int f : path) {
+                col[f] = col[f] == a ? b : a;
+                at_r[edges[f].first * delta + col[f]] = f;
+                at_g[edges[f].second * delta + col[f]] = f;
+            }
+        }
+        col[e] = a;
+        at_r[r * delta + a] = (int)e;
+        at_g[g * delta + a] = (int)e;
+    }
+    return col;
+}
+
+// Orders one precode row's member slots into octets (8 lanes of a quarter
+// warp) that repeat a bank group as little as possible: each octet first
+// takes one member from each group, fullest groups first. The last octet is
+// filled with zero slots (zbase + group) of groups it does not use.
+void pack_octets(std::vector<uint16_t> members, int32_t zbase, std::vector<uint16_t> &out) {
+    std::vector<uint16_t> by[8];
+    for (uint16_t s : members) by[bank_group(s)].push_back(s);
+    size_t left = members.size();
+    while (left) {
+        int taken = 0;
+        while (taken < 8 && left) {
+            int order[8];
+            std::iota(order, order + 8, 0);
+            std::stable_sort(order, order + 8,
+                             [&](int x, int y) { return by[x].size() > by[y].size(); });
+            for (int i = 0; i < 8 && taken < 8; ++i) {
+                std::vector<uint16_t> &l = by[order[i]];
+                if (l.empty()) break;
+                out.push_back(l.back());
+                l.pop_back();
+                ++taken;
+                --left;
+            }
+        }
+        if (taken < 8) {  // last octet: zero slots in the groups it leaves free
+            bool used[8] = {false};
+            for (size_t i = out.size() - taken; i < out.size(); ++i) used[bank_group(out[i])] = true;
+            for (int k = 0; k < 8 && taken < 8; ++k)
+                if (!used[k]) {
+                    out.push_back((uint16_t)(zbase + k));
+                    ++taken;
+                }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t *con_idx) {
+    c->sl_slots = 0;
+    if (c->b < 1 || c->n < 1 || c->n >= kNoSlot) return cudaSuccess;
+    const int32_t box_rows = c->b < 256 ? c->b : 256;
+    const int64_t bpad = ((int64_t)c->b + box_rows - 1) / box_rows * box_rows;
+    // data slots, parity slots, then 8 zero slots (one per bank group)
+    const int64_t zbase = (bpad + c->m + 7) & ~(int64_t)7;
+    const int64_t slots = zbase + 8;
+    if (slots >= kNoSlot) return cudaSuccess;
+    auto slot_of = [&](int32_t v) -> uint16_t {
+        return (uint16_t)(v < c->b ? v : bpad + (v - c->b));
+    };
+    const int32_t n = c->n;
+    auto deg = [&](int32_t r) { return con_ptr[r + 1] - con_ptr[r]; };
+
+    // coded rows into quarters of 8: rows of about the same degree (largest
+    // first) whose neighbours spread evenly over the bank groups
+    std::vector<int32_t> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return deg(x) > deg(y); });
+    std::vector<char> used(n, 0);
+    struct Quarter {
+        int32_t row[8];
+        int delta;
+    };
+    std::vector<Quarter> quarters;
+    constexpr int kWindow = 64;  // candidates looked at for each place
+    size_t pos = 0;
+    for (;;) {
+        while (pos < (size_t)n && used[order[pos]]) ++pos;
+        if (pos >= (size_t)n) break;
+        Quarter q;
+        std::fill(q.row, q.row + 8, -1);
+        int cnt[8] = {0};
+        int dmax = deg(order[pos]);
+        for (int k = 0; k < 8; ++k) {
+            int32_t best = -1;
+            int best_key = 0, best_deg = 0;
+            int seen = 0;
+            for (size_t i = pos; i < (size_t)n && seen < (k == 0 ? 1 : kWindow); ++i) {
+                const int32_t r = order[i];
+                if (used[r]) continue;
+                ++seen;
+                int c2[8];
+                std::copy(cnt, cnt + 8, c2);
+                for (int32_t e = con_ptr[r]; e < con_ptr[r + 1]; ++e) ++c2[bank_group(slot_of(con_idx[e]))];
+                const int key = std::max(*std::max_element(c2, c2 + 8), dmax);
+                if (best < 0 || key < best_key || (key == best_key && deg(r) > best_deg)) {
+                    best = r;
+                    best_key = key;
+                    best_deg = deg(r);
+                }
+            }
+            if (best < 0) break;
+            used[best] = 1;
+            q.row[k] = best;
+            for (int32_t e = con_ptr[best]; e < con_ptr[best + 1]; ++e)
+                ++cnt[bank_group(slot_of(con_idx[e]))];
+        }
+        q.delta = std::max(*std::max_element(cnt, cnt + 8), dmax);
+        quarters.push_back(q);
+    }
+    std::stable_sort(quarters.begin(), quarters.end(),
+                     [](const Quarter &x, const Quarter &y) { return x.delta > y.delta; });
+    const int32_t n_grp = (int32_t)((quarters.size() + 3) / 4);
+    std::vector<int2> grp(n_grp);
+    int64_t total = 0;
+    for (int32_t gq = 0; gq < n_grp; ++gq) {
+        const int cols = quarters[(size_t)gq * 4].delta;  // sorted: the first is the widest
+        grp[gq] = make_int2((int32_t)total, cols);
+        total += 32 * (int64_t)cols;
+        if (total > (int64_t)1 << 24) return cudaSuccess;
+    }
+    // precode rows: members (the joint graph's check rows end with their own
+    // parity, left out) packed into octets
+    std::vector<int32_t> pptr((size_t)c->m + 1, 0);
+    std::vector<uint16_t> pre;
+    for (int32_t j = 0; j < c->m; ++j) {
+        const int32_t g = n + j;
+        std::vector<uint16_t> mem;
+        for (int32_t e = con_ptr[g]; e < con_ptr[g + 1] - 1; ++e) mem.push_back(slot_of(con_idx[e]));
+        pack_octets(std::move(mem), (int32_t)zbase, pre);
+        pptr[j + 1] = (int32_t)pre.size();
+    }
+
+    auto al16 = [](int64_t x) { return (x + 15) & ~(int64_t)15; };
+    const int64_t off_row = al16((int64_t)sizeof(int2) * n_grp);
+    const int64_t off_pptr = al16(off_row + 2 * 32 * (int64_t)n_grp);
+    const int64_t off_pre = al16(off_pptr + 4 * ((int64_t)c->m + 1));
+    const int64_t off_idx = al16(off_pre + 2 * (int64_t)pre.size());
+    const int64_t bytes = al16(off_idx + 2 * total);
+    if ((size_t)slots * 16 + (size_t)bytes + 1024 > c->smem_optin) return cudaSuccess;
+
+    std::vector<unsigned char> tab((size_t)bytes, 0);
+    memcpy(tab.data(), grp.data(), sizeof(int2) * n_grp);
+    uint16_t *row = reinterpret_cast<uint16_t *>(tab.data() + off_row);
+    int32_t *tp = reinterpret_cast<int32_t *>(tab.data() + off_pptr);
+    uint16_t *tpre = reinterpret_cast<uint16_t *>(tab.data() + off_pre);
+    uint16_t *idx = reinterpret_cast<uint16_t *>(tab.data() + off_idx);
+    std::fill(row, row + 32 * (size_t)n_grp, kNoSlot);
+    std::fill(idx, idx + total, kNoSlot);
+    std::copy(pptr.begin(), pptr.end(), tp);
+    std::copy(pre.begin(), pre.end(), tpre);
+    std::vector<std::pair<int, int>> edges;
+    std::vector<uint16_t> eslot;
+    for (size_t qi = 0; qi < quarters.size(); ++qi) {
+        const Quarter &q = quarters[qi];
+        const int32_t gq = (int32_t)(qi / 4), lane0 = 8 * (int32_t)(qi % 4);
+        edges.clear();
+        eslot.clear();
+        for (int p = 0; p < 8; ++p) {
+            if (q.row[p] < 0) continue;
+            row[(size_t)gq * 32 + lane0 + p] = (uint16_t)q.row[p];
+            for (int32_t e = con_ptr[q.row[p]]; e < con_ptr[q.row[p] + 1]; ++e) {
+                const uint16_t sl = slot_of(con_idx[e]);
+                edges.emplace_back(p, bank_group(sl));
+                eslot.push_back(sl);
+            }
+        }
+        const std::vector<int> col = colour_edges(edges, std::max(q.delta, 1));
+        for (size_t e = 0; e < edges.size(); ++e)
+            idx[(size_t)grp[gq].x + (size_t)col[e] * 32 + lane0 + edges[e].first] = eslot[e];
+        // empty cells of each column: the zero slot of a group the column leaves free
+        for (int cc = 0; cc < grp[gq].y; ++cc) {
+            uint16_t *cell = idx + (size_t)grp[gq].x + (size_t)cc * 32 + lane0;
+            bool used[8] = {false};
+            for (int p = 0; p < 8; ++p)
+                if (cell[p] != kNoSlot) used[bank_group(cell[p])] = true;
+            int k = 0;
+            for (int p = 0; p < 8; ++p) {
+                if (cell[p] != kNoSlot) continue;
+                while (k < 7 && used[k]) ++k;
+                cell[p] = (uint16_t)(zbase + k);
+            }
+        }
+    }
+    // quarters of the last group that hold no rows
+    for (size_t qi = quarters.size(); qi < 4 * (size_t)n_grp; ++qi)
+        for (int cc = 0; cc < grp[qi / 4].y; ++cc)
+            for (int p = 0; p < 8; ++p)
+                idx[(size_t)grp[qi / 4].x + (size_t)cc * 32 + 8 * (qi % 4) + p] = (uint16_t)(zbase + p);
+
+    cudaError_t e = cudaMalloc(&c->sl_tab, (size_t)bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(c->sl_tab, tab.data(), (size_t)bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    c->sl_box_rows = box_rows;
+    c->sl_bpad = (int32_t)bpad;
+    c->sl_n_grp = n_grp;
+    c->sl_tab_bytes = (int32_t)bytes;
+    c->sl_off_row = (int32_t)off_row;
+    c->sl_off_pptr = (int32_t)off_pptr;
+    c->sl_off_pre = (int32_t)off_pre;
+    c->sl_off_idx = (int32_t)off_idx;
+    c->sl_zbase = (int32_t)zbase;
+    c->sl_slots = (int32_t)slots;
+    return cudaSuccess;
+}
+
+void free_slice_tables(fs_code *c) { cudaFree(c->sl_tab); }
+
+namespace {
+
+// Slice encode of the whole code; false (nothing launched) when it does not apply.
+// Two slot buffers (the next slice's copies land under the current slice's
+// arithmetic) matter more than the slot width, so: 32-byte slots (full-sector
+// copies and stores) when two buffers of them fit, else 16-byte slots, with
+// two buffers when they fit.
+bool launch_slices(const fs_code *c, const void *data, void *parity, void *coded, int32_t *hdr,
+                   cudaStream_t s, cudaError_t *err) {
+    *err = cudaSuccess;
+    if (!c->encode_slices || c->sl_slots == 0 || c->t >= ((int64_t)1 << 31)) return false;
+    EncodeTiledFn encode = tensor_map_encoder();
+    if (!encode) return false;
+    int v = c->encode_slices == 2   ? 1
+            : c->encode_slices == 3 ? 2
+            : (slice_smem_bytes(c, 2, 2) <= c->smem_optin && c->tw >= 2 ? 2 : 1);
+    if (slice_smem_bytes(c, v, 1) > c->smem_optin) v = 1;
+    const int nbuf = slice_smem_bytes(c, v, 2) <= c->smem_optin ? 2 : 1;
+    const size_t smem = slice_smem_bytes(c, v, nbuf);
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)c->t, (cuuint64_t)c->b};
+    const cuuint64_t strides[1] = {(cuuint64_t)c->t};
+    const cuuint32_t box[2] = {(cuuint32_t)(16 * v), (cuuint32_t)c->sl_box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(data), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               v == 2 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    SliceArgs a;
+    a.tab = reinterpret_cast<const uint4 *>(c->sl_tab);
+    a.tab_words = c->sl_tab_bytes / 16;
+    a.off_row = c->sl_off_row;
+    a.off_pptr = c->sl_off_pptr;
+    a.off_pre = c->sl_off_pre;
+    a.off_idx = c->sl_off_idx;
+    a.parity = static_cast<uint4 *>(parity);
+    a.coded = static_cast<uint4 *>(coded);
+    a.m = c->m;
+    a.n_grp = c->sl_n_grp;
+    a.bpad = c->sl_bpad;
+    a.zbase = c->sl_zbase;
+    a.slots = c->sl_slots;
+    a.box_rows = c->sl_box_rows;
+    a.n_boxes = c->sl_bpad / c->sl_box_rows;
+    a.nbuf = nbuf;
+    a.tw = c->tw;
+    a.n_slices = (int32_t)((c->tw + v - 1) / v);
+    a.ticket = hdr + WS_COUNT_A;
+    a.status = hdr + WS_STATUS;
+    auto kern = v == 2 ? k_slices<2> : k_slices<1>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        const int64_t g = a.n_slices < c->num_sms ? a.n_slices : c->num_sms;
+        kern<<<(int)(g < 1 ? 1 : g), kSliceThreads, smem, s>>>(map, a);
+        e = cudaGetLastError();
+    }
+    *err = e;
+    return true;
+}
+
+}  // namespace
+
 cudaError_t launch_encode(const fs_code *c, const void *data, void *parity, void *coded, uint8_t *ws,
                           cudaStream_t s) {
     int32_t *hdr = reinterpret_cast<int32_t *>(ws);
-    // status (nothing here can fail on the device) and both ticket counters
+    // status and the ticket counters
     cudaError_t e = cudaMemsetAsync(ws, 0, WS_HDR_BYTES, s);
     if (e != cudaSuccess) return e;
+    if (launch_slices(c, data, parity, coded, hdr, s, &e)) return e;
     const int32_t n_chunks = encode_chunks(c);
     const int ctas = c->gather_ctas < kCtasPerSm ? c->gather_ctas : kCtasPerSm;
     RowArgs a;
     a.tw = c->tw;
     a.n_chunks = n_chunks;
+    a.hints = c->l2_hints;
     if (c->m > 0) {  // step (1): parities over the data blocks
         a.ptr = c->pre_ptr;
         a.idx = c->pre_idx;

@@ -39,7 +39,32 @@ struct fs_code {
     int peel_ctas;        // payload-peel CTAs per SM (slice width follows)
     int gather_ctas;      // resident CTAs per SM for the gather kernels
     int dpg_compact;      // 1: symbolic peel in the compact shared-memory form when it fits
+    int l2_hints;         // 1: L2 evict-last / evict-first hints on the gathers
+    int encode_slices;    // 1: shared-memory slice encode when the code fits
+    // slice encode tables (present when sl_slots > 0): every input block has
+    // a 16-byte shared-memory slot per byte slice; data block v is slot v,
+    // parity j is slot sl_bpad + j
+    int32_t sl_box_rows;  // rows of one TMA box (data blocks per copy)
+    int32_t sl_bpad;      // data slots, b rounded up to sl_box_rows
+    int32_t sl_zbase;     // first of 8 zero slots (one per bank group), after the parities
+    int32_t sl_slots;     // slots of one buffer (sl_zbase + 8)
+    int32_t sl_n_grp;     // warp groups of 32 coded rows, by degree
+    // one device array holding the tables the kernel copies to shared
+    // memory, each part starting on a 16-byte boundary:
+    //   grp   int2 [sl_n_grp]       {first entry, degree of the group}
+    //   row   uint16 [32 sl_n_grp]  coded row of each lane, 0xFFFF pad
+    //   pptr  int32 [m + 1]         precode row starts
+    //   pre   uint16 [e_pre]        precode members as slots
+    //   idx   uint16 [...]          group entries, column-major, 0xFFFF pad
+    unsigned char *sl_tab;
+    int32_t sl_tab_bytes;  // multiple of 16
+    int32_t sl_off_row, sl_off_pptr, sl_off_pre, sl_off_idx;  // byte offsets
 };
+
+// Builds the slice encode tables of c (host arrays of the joint graph);
+// leaves sl_slots = 0 when the code does not fit.
+cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t *con_idx);
+void free_slice_tables(fs_code *c);
 
 constexpr int kRecipeSeg = 8;  // recipe entries one payload thread gathers at once
 
@@ -123,6 +148,43 @@ static inline UpdateLayout update_layout(const fs_code *c, int32_t n_items) {
     L.total = o;
     return L;
 }
+
+// ---- L2 eviction-priority hints -------------------------------------------
+// A cache policy (createpolicy) marks the lines an access brings into L2 as
+// evict-last (data read again later in the same launch) or evict-first
+// (data streamed through once). Used only where the tuning knob enables it.
+#ifdef __CUDACC__
+__device__ __forceinline__ uint64_t l2_policy_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint4 ld_nc_hint(const uint4 *ptr, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;\n"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint4 ld_hint(const uint4 *ptr, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;\n"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(ptr), "l"(pol)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_hint(uint4 *ptr, const uint4 &v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;\n" ::"l"(ptr),
+                 "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+}
+#endif
 
 // ---- kernel launchers (return cudaError_t of the launch) ----------------
 // Gather-XOR over CSR rows: out row r = XOR of input blocks idx[ptr[r]..ptr[r+1]).

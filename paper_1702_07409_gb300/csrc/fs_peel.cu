@@ -621,6 +621,7 @@ struct PeelArgs {
     int32_t b, n;
     int64_t tw;
     int32_t L;  // words of every block per CTA
+    int32_t hints;  // 1: gathered / recovered blocks evict-last, coded payloads evict-first
     int32_t *status;
 };
 
@@ -827,6 +828,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             cp_async_commit();
             const int4 lt = ltab[2 * l];
             const int np = lt.y, ns = lt.w;
+            const uint64_t pol_last = l2_policy_last(), pol_first = l2_policy_first();
             // every (segment, word pair): one gather of at most kRecipeSeg blocks
             for (int it = threadIdx.x; it < ns * nv; it += blockDim.x) {
                 const int s = it / nv, k = it - s * nv;
@@ -840,8 +842,8 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 uint4 acc0 = make_uint4(0, 0, 0, 0), acc1 = acc0;
                 if (sidx == 0 && g < a.n) {
                     const uint4 *src = a.coded + (int64_t)g * a.tw + w;
-                    acc0 = src[0];
-                    if (two) acc1 = src[1];
+                    acc0 = a.hints ? ld_nc_hint(src, pol_first) : src[0];
+                    if (two) acc1 = a.hints ? ld_nc_hint(src + 1, pol_first) : src[1];
                 }
                 uint4 x0[kRecipeSeg], x1[kRecipeSeg];
 #pragma unroll
@@ -850,8 +852,8 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                     x0[j] = x1[j] = make_uint4(0, 0, 0, 0);
                     if (h >= 0 && h != f) {
                         const uint4 *src = block_ptr(a, h) + w;
-                        x0[j] = src[0];
-                        if (two) x1[j] = src[1];
+                        x0[j] = a.hints ? ld_hint(src, pol_last) : src[0];
+                        if (two) x1[j] = a.hints ? ld_hint(src + 1, pol_last) : src[1];
                     }
                 }
 #pragma unroll
@@ -861,8 +863,13 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
                 }
                 if (slot < 0) {
                     uint4 *dst = block_ptr(a, f) + w;
-                    dst[0] = acc0;
-                    if (two) dst[1] = acc1;
+                    if (a.hints) {
+                        st_hint(dst, acc0, pol_last);
+                        if (two) st_hint(dst + 1, acc1, pol_last);
+                    } else {
+                        dst[0] = acc0;
+                        if (two) dst[1] = acc1;
+                    }
                 } else {  // one of several segments: combine in shared memory
                     xor_shared(accs + slot * L + k * kPeelV, acc0);
                     if (two) xor_shared(accs + slot * L + k * kPeelV + 1, acc1);
@@ -971,6 +978,7 @@ cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, u
     a.b = c->b;
     a.n = c->n;
     a.tw = c->tw;
+    a.hints = c->l2_hints;
     a.status = reinterpret_cast<int32_t *>(ws) + WS_STATUS;
     // slice width: every slice in flight at once (peel_ctas CTAs per SM),
     // a whole number of word pairs, at most kPeelLmax words

@@ -1,8 +1,8 @@
 // fs_static.cu - fs_encode_static: the encode entry point for callers that
 // cannot allocate device memory.
 //
-// fs_encode needs a small caller-provided workspace (a status word, a tile
-// counter and one counter per byte chunk). Some callers have no way to
+// fs_encode needs a small caller-provided workspace (a status word and the
+// work-ticket counters of its kernels). Some callers have no way to
 // provide one: a storage service that reserves all of its device memory at
 // start-up and forbids any later allocation (cudaMalloc may synchronise the
 // device and can fail under memory pressure in the middle of a request), or

@@ -19,7 +19,8 @@ FS_OK, FS_STALL, FS_ERR_INVALID, FS_ERR_CUDA, FS_ERR_NOMEM, FS_ERR_TIMEOUT, FS_E
 ENCODE_STATIC_SCRATCH_BYTES = 65536
 DECODE_JOINT, DECODE_TWO_PASS = 0, 1
 OP_ENCODE, OP_DECODE, OP_UPDATE, OP_REPAIR = 0, 1, 2, 3
-TUNE_PEEL_CTAS, TUNE_GATHER_CTAS, TUNE_DPG_COMPACT = 1, 2, 3
+TUNE_PEEL_CTAS, TUNE_GATHER_CTAS, TUNE_DPG_COMPACT, TUNE_L2_HINTS = 1, 2, 3, 4
+TUNE_ENCODE_SLICES = 5
 WS_STATUS_OFFSET = 0
 
 #: every symbol declared in include/founsure_gpu.h

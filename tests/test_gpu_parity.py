@@ -283,10 +283,12 @@ def test_long_chain_takes_the_direct_path():
     assert path.n_levels == b
 
 
-@pytest.mark.parametrize("knob,value", [(1, 2), (1, 4), (2, 1), (3, 0)])
+@pytest.mark.parametrize("knob,value", [(1, 2), (1, 4), (2, 1), (3, 0), (4, 1), (5, 0), (5, 2),
+                                        (5, 3)])
 def test_tuning_knobs_leave_results_unchanged(knob, value):
     """Payload CTAs per SM, one gather CTA per SM, general (not compact)
-    decoding schedule."""
+    decoding schedule, L2 eviction hints, row-gather encode, 16- and 32-byte
+    slice encode."""
     import torch
     fs = _fs()
     case = Case(1500, 60, 2000, 4096 + 32, gen.DIST_FINITE40)
