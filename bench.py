@@ -182,8 +182,8 @@ class Stripe:
         self.host_nun = torch.empty(1, dtype=torch.int32).pin_memory()
         self.nun_reads = []
 
-    # launches of this library's kernels per step (encode 2, decode 2,
-    # update 5, repair 1)
+    # launches of this library's kernels per step (encode 1: the slice
+    # kernel; decode 2: schedule + payload; update 6; repair 1)
     LAUNCHES_PER_STEP = 10
 
     def step(self, r: int, ev=None):

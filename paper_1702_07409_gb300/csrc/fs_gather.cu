@@ -1,16 +1,21 @@
 // fs_gather.cu - region-XOR gather kernels: encode (Section 2.2 steps (1)
 // and (2)), conventional repair (Section 4) and the delta-XOR update.
 //
-// Work unit: a tile = (CSR row r, byte chunk) of one output block. Tiles are
-// numbered chunk-major, so the CTAs resident at one time all work on the same
-// byte range of every block: the gathered inputs of that range (k_int blocks
-// x one chunk) stay in L2 while the rows that share them are computed, and
-// each input byte is fetched from HBM about once per launch.
+// Work unit: a tile = (CSR row r, byte chunk of 16 KiB) of one output block.
+// A tile first lists its sources (the row's neighbours; for the update only
+// the neighbours that changed) as block pointers in shared memory, then every
+// thread streams 4 words from each source, two sources at a time, so each
+// thread keeps 8 independent 16-byte loads in flight. Tiles are numbered
+// chunk-major, so the CTAs resident at one time work on about the same byte
+// range of every block.
 #include "fs_internal.cuh"
 
 namespace {
 
-constexpr int kGatherThreads = 256;  // one 16-byte word per thread per chunk
+constexpr int kGatherThreads = 256;
+constexpr int kWpt = 4;                             // 16-byte words per thread per tile
+constexpr int kChunkW = kGatherThreads * kWpt;      // words per tile (16 KiB)
+constexpr int kSrcBatch = kGatherThreads;           // sources listed at a time
 constexpr int kCtasPerSm = 8;
 
 __device__ __forceinline__ void xor4(uint4 &a, const uint4 &b) {
@@ -24,8 +29,41 @@ __device__ __forceinline__ const uint4 *in_block(const GatherArgs &a, int32_t v)
     return (v < a.split) ? a.inA + (int64_t)v * a.tw : a.inB + (int64_t)(v - a.split) * a.tw;
 }
 
-__global__ void __launch_bounds__(kGatherThreads)
-k_gather_xor(GatherArgs a, int32_t chunk_w, int32_t n_chunks) {
+// acc[i] ^= src[k][w0 + threadIdx.x + i * blockDim.x] over the n listed sources
+__device__ __forceinline__ void xor_sources(uint4 *acc, const uint4 *const *src, int n, int64_t w0,
+                                            int64_t w1) {
+    int64_t w[kWpt];
+    bool ok[kWpt];
+#pragma unroll
+    for (int i = 0; i < kWpt; ++i) {
+        w[i] = w0 + threadIdx.x + (int64_t)i * kGatherThreads;
+        ok[i] = w[i] < w1;
+    }
+    int k = 0;
+    for (; k + 2 <= n; k += 2) {
+        const uint4 *s0 = src[k], *s1 = src[k + 1];
+        uint4 x0[kWpt], x1[kWpt];
+#pragma unroll
+        for (int i = 0; i < kWpt; ++i) {
+            x0[i] = ok[i] ? __ldg(s0 + w[i]) : make_uint4(0, 0, 0, 0);
+            x1[i] = ok[i] ? __ldg(s1 + w[i]) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int i = 0; i < kWpt; ++i) {
+            xor4(acc[i], x0[i]);
+            xor4(acc[i], x1[i]);
+        }
+    }
+    if (k < n) {
+#pragma unroll
+        for (int i = 0; i < kWpt; ++i)
+            if (ok[i]) xor4(acc[i], __ldg(src[k] + w[i]));
+    }
+}
+
+__global__ void __launch_bounds__(kGatherThreads, 4)
+k_gather_xor(GatherArgs a, int32_t n_chunks) {
+    __shared__ const uint4 *s_src[kSrcBatch];
     // without a row list nothing here can fail: report a clean call
     if (!a.rows && blockIdx.x == 0 && threadIdx.x == 0) *a.status = FS_OK;
     const int64_t n_tiles = (int64_t)n_chunks * a.n_rows;
@@ -35,32 +73,29 @@ k_gather_xor(GatherArgs a, int32_t chunk_w, int32_t n_chunks) {
         int32_t row = a.row_base + r;
         if (a.rows) {
             row = __ldg(a.rows + r);
-            if (row < 0 || row >= a.n_valid) {
+            if (row < 0 || row >= a.n_valid) {  // the same decision in every thread
                 if (threadIdx.x == 0 && chunk == 0) atomicExch(a.status, FS_ERR_INVALID);
                 continue;
             }
         }
         const int32_t e0 = __ldg(a.ptr + row), e1 = __ldg(a.ptr + row + 1);
-        const int64_t w0 = (int64_t)chunk * chunk_w;
-        const int64_t w1 = min(w0 + chunk_w, a.tw);
+        const int64_t w0 = (int64_t)chunk * kChunkW;
+        const int64_t w1 = min(w0 + kChunkW, a.tw);
+        uint4 acc[kWpt];
+#pragma unroll
+        for (int i = 0; i < kWpt; ++i) acc[i] = make_uint4(0, 0, 0, 0);
+        for (int32_t base = e0; base < e1; base += kSrcBatch) {
+            const int nb = min(kSrcBatch, e1 - base);
+            __syncthreads();  // the previous batch is consumed
+            if ((int)threadIdx.x < nb) s_src[threadIdx.x] = in_block(a, __ldg(a.idx + base + threadIdx.x));
+            __syncthreads();
+            xor_sources(acc, s_src, nb, w0, w1);
+        }
         uint4 *dst = a.out + (int64_t)row * a.tw;
-        for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
-            uint4 acc = make_uint4(0, 0, 0, 0);
-            int32_t e = e0;
-            for (; e + 4 <= e1; e += 4) {
-                const int32_t v0 = __ldg(a.idx + e), v1 = __ldg(a.idx + e + 1);
-                const int32_t v2 = __ldg(a.idx + e + 2), v3 = __ldg(a.idx + e + 3);
-                const uint4 x0 = __ldg(in_block(a, v0) + w);
-                const uint4 x1 = __ldg(in_block(a, v1) + w);
-                const uint4 x2 = __ldg(in_block(a, v2) + w);
-                const uint4 x3 = __ldg(in_block(a, v3) + w);
-                xor4(acc, x0);
-                xor4(acc, x1);
-                xor4(acc, x2);
-                xor4(acc, x3);
-            }
-            for (; e < e1; ++e) xor4(acc, __ldg(in_block(a, __ldg(a.idx + e)) + w));
-            __stcs(dst + w, acc);
+#pragma unroll
+        for (int i = 0; i < kWpt; ++i) {
+            const int64_t w = w0 + threadIdx.x + (int64_t)i * kGatherThreads;
+            if (w < w1) __stcs(dst + w, acc[i]);
         }
     }
 }
@@ -123,21 +158,32 @@ __device__ __forceinline__ void touch(const UpdArgs &a, int32_t c, bool coded_on
 // Tiles (q, chunk): delta_q = old ^ new and data block idx[q] <- new over
 // the chunk; the chunk-0 tile of q also lists every constraint containing
 // that block (coded rows and checks).
-__global__ void __launch_bounds__(kGatherThreads)
-k_update_delta(UpdArgs a, int32_t chunk_w, int32_t n_chunks) {
+__global__ void __launch_bounds__(kGatherThreads, 4)
+k_update_delta(UpdArgs a, int32_t n_chunks) {
     if (!upd_ok(a)) return;
     const int64_t n_tiles = (int64_t)a.n_idx * n_chunks;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int32_t q = (int32_t)(tile / n_chunks);
         const int32_t chunk = (int32_t)(tile - (int64_t)q * n_chunks);
         const int32_t i = a.idx[q];
-        const int64_t w0 = (int64_t)chunk * chunk_w, w1 = min(w0 + chunk_w, a.tw);
-        for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
-            const uint4 nw = __ldg(a.d_new + (int64_t)q * a.tw + w);
-            uint4 d = a.data[(int64_t)i * a.tw + w];
-            xor4(d, nw);
-            a.delta[(int64_t)q * a.tw + w] = d;
-            a.data[(int64_t)i * a.tw + w] = nw;
+        const int64_t w0 = (int64_t)chunk * kChunkW, w1 = min(w0 + kChunkW, a.tw);
+        uint4 nw[kWpt], d[kWpt];
+#pragma unroll
+        for (int k = 0; k < kWpt; ++k) {
+            const int64_t w = w0 + threadIdx.x + (int64_t)k * kGatherThreads;
+            if (w < w1) {
+                nw[k] = __ldg(a.d_new + (int64_t)q * a.tw + w);
+                d[k] = a.data[(int64_t)i * a.tw + w];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kWpt; ++k) {
+            const int64_t w = w0 + threadIdx.x + (int64_t)k * kGatherThreads;
+            if (w < w1) {
+                xor4(d[k], nw[k]);
+                a.delta[(int64_t)q * a.tw + w] = d[k];
+                a.data[(int64_t)i * a.tw + w] = nw[k];
+            }
         }
         if (chunk == 0)
             for (int32_t e = a.var_ptr[i] + threadIdx.x; e < a.var_ptr[i + 1]; e += blockDim.x)
@@ -156,13 +202,35 @@ __global__ void k_update_plist(UpdArgs a) {
     }
 }
 
+// Lists, in s_src, the deltas of the changed members among con_idx-style
+// entries [base, base + nb) (data block v: its delta if it was rewritten;
+// v >= b: parity v - b's delta if that check changed). Returns the count.
+__device__ __forceinline__ int list_changed(const UpdArgs &a, const int32_t *members, int32_t base,
+                                            int nb, const uint4 **s_src, int *s_n) {
+    __syncthreads();  // the previous list is consumed
+    if (threadIdx.x == 0) *s_n = 0;
+    __syncthreads();
+    if ((int)threadIdx.x < nb) {
+        const int32_t v = members[base + threadIdx.x];
+        const uint4 *p = nullptr;
+        if (v < a.b) {
+            const int32_t q = a.mark[v];
+            if (q >= 0) p = a.delta + (int64_t)q * a.tw;
+        } else if (a.pmark[v - a.b]) {
+            p = a.pdelta + (int64_t)(v - a.b) * a.tw;
+        }
+        if (p) s_src[atomicAdd(s_n, 1)] = p;
+    }
+    __syncthreads();
+    return *s_n;
+}
+
 // changed parity j ^= XOR of the deltas of its changed members; pdelta_j
-// keeps that XOR. Tiles (listed check, chunk), chunk-major. Warp 0 first
-// lists the changed members of the check (32 members per step, ballot).
-__global__ void __launch_bounds__(kGatherThreads)
-k_update_parity(UpdArgs a, int32_t chunk_w, int32_t n_chunks) {
-    __shared__ int32_t s_q[kGatherThreads];
-    __shared__ int s_nq, s_ok;
+// keeps that XOR. Tiles (listed check, chunk), chunk-major.
+__global__ void __launch_bounds__(kGatherThreads, 3)
+k_update_parity(UpdArgs a, int32_t n_chunks) {
+    __shared__ const uint4 *s_src[kSrcBatch];
+    __shared__ int s_n, s_ok;
     if (threadIdx.x == 0) s_ok = upd_ok(a);  // one decision for the whole CTA
     __syncthreads();
     if (!s_ok) return;
@@ -172,77 +240,61 @@ k_update_parity(UpdArgs a, int32_t chunk_w, int32_t n_chunks) {
         const int32_t chunk = (int32_t)(tile / np);
         const int32_t j = a.plist[tile - (int64_t)chunk * np];
         const int32_t e0 = a.pre_ptr[j], e1 = a.pre_ptr[j + 1];
-        const int64_t w0 = (int64_t)chunk * chunk_w, w1 = min(w0 + chunk_w, a.tw);
-        if (threadIdx.x < 32) {
-            int nq = 0;
-            for (int32_t base = e0; base < e1; base += 32) {
-                const int32_t e = base + (int32_t)threadIdx.x;
-                const int32_t q = e < e1 ? a.mark[a.pre_idx[e]] : -1;
-                const unsigned hit = __ballot_sync(0xffffffffu, q >= 0);
-                const int pos = nq + __popc(hit & ((1u << threadIdx.x) - 1u));
-                if (q >= 0 && pos < kGatherThreads) s_q[pos] = q;
-                nq += __popc(hit);
-            }
-            if (threadIdx.x == 0) s_nq = nq;
+        const int64_t w0 = (int64_t)chunk * kChunkW, w1 = min(w0 + kChunkW, a.tw);
+        uint4 acc[kWpt];
+#pragma unroll
+        for (int i = 0; i < kWpt; ++i) acc[i] = make_uint4(0, 0, 0, 0);
+        for (int32_t base = e0; base < e1; base += kSrcBatch) {
+            const int n = list_changed(a, a.pre_idx, base, min(kSrcBatch, e1 - base), s_src, &s_n);
+            xor_sources(acc, s_src, n, w0, w1);
         }
-        __syncthreads();
-        const int nq = s_nq;
-        for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
-            uint4 acc = make_uint4(0, 0, 0, 0);
-            if (nq <= kGatherThreads) {
-                for (int k = 0; k < nq; ++k) xor4(acc, a.delta[(int64_t)s_q[k] * a.tw + w]);
-            } else {  // more changed members than the list holds: scan the check
-                for (int32_t e = e0; e < e1; ++e) {
-                    const int32_t q = a.mark[a.pre_idx[e]];
-                    if (q >= 0) xor4(acc, a.delta[(int64_t)q * a.tw + w]);
-                }
-            }
-            a.pdelta[(int64_t)j * a.tw + w] = acc;
+#pragma unroll
+        for (int i = 0; i < kWpt; ++i) {
+            const int64_t w = w0 + threadIdx.x + (int64_t)i * kGatherThreads;
+            if (w >= w1) continue;
+            a.pdelta[(int64_t)j * a.tw + w] = acc[i];
             uint4 p = a.parity[(int64_t)j * a.tw + w];
-            xor4(p, acc);
+            xor4(p, acc[i]);
             a.parity[(int64_t)j * a.tw + w] = p;
         }
-        __syncthreads();
     }
 }
 
 // listed coded row g ^= XOR of the deltas of its changed neighbours (data
 // blocks and parities). Tiles (listed row, chunk), chunk-major.
-__global__ void __launch_bounds__(kGatherThreads)
-k_update_coded(UpdArgs a, int32_t chunk_w, int32_t n_chunks) {
-    if (!upd_ok(a)) return;
+__global__ void __launch_bounds__(kGatherThreads, 3)
+k_update_coded(UpdArgs a, int32_t n_chunks) {
+    __shared__ const uint4 *s_src[kSrcBatch];
+    __shared__ int s_n, s_ok;
+    if (threadIdx.x == 0) s_ok = upd_ok(a);
+    __syncthreads();
+    if (!s_ok) return;
     const int32_t nc = *(volatile int32_t *)a.n_clist;
     const int64_t n_tiles = (int64_t)n_chunks * nc;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int32_t chunk = (int32_t)(tile / nc);
         const int32_t g = a.clist[tile - (int64_t)chunk * nc];
         const int32_t e0 = a.con_ptr[g], e1 = a.con_ptr[g + 1];
-        const int64_t w0 = (int64_t)chunk * chunk_w, w1 = min(w0 + chunk_w, a.tw);
-        for (int64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
-            uint4 acc = make_uint4(0, 0, 0, 0);
-            for (int32_t e = e0; e < e1; ++e) {
-                const int32_t v = a.con_idx[e];
-                if (v < a.b) {
-                    const int32_t q = a.mark[v];
-                    if (q >= 0) xor4(acc, a.delta[(int64_t)q * a.tw + w]);
-                } else if (a.pmark[v - a.b]) {
-                    xor4(acc, a.pdelta[(int64_t)(v - a.b) * a.tw + w]);
-                }
-            }
-            uint4 c = a.coded[(int64_t)g * a.tw + w];
-            xor4(c, acc);
-            a.coded[(int64_t)g * a.tw + w] = c;
+        const int64_t w0 = (int64_t)chunk * kChunkW, w1 = min(w0 + kChunkW, a.tw);
+        uint4 acc[kWpt];
+#pragma unroll
+        for (int i = 0; i < kWpt; ++i) {
+            const int64_t w = w0 + threadIdx.x + (int64_t)i * kGatherThreads;
+            acc[i] = w < w1 ? a.coded[(int64_t)g * a.tw + w] : make_uint4(0, 0, 0, 0);
+        }
+        for (int32_t base = e0; base < e1; base += kSrcBatch) {
+            const int n = list_changed(a, a.con_idx, base, min(kSrcBatch, e1 - base), s_src, &s_n);
+            xor_sources(acc, s_src, n, w0, w1);
+        }
+#pragma unroll
+        for (int i = 0; i < kWpt; ++i) {
+            const int64_t w = w0 + threadIdx.x + (int64_t)i * kGatherThreads;
+            if (w < w1) a.coded[(int64_t)g * a.tw + w] = acc[i];
         }
     }
 }
 
-inline void chunking(int64_t tw, int32_t *chunk_w, int32_t *n_chunks, int *threads) {
-    const int64_t cw = tw < kGatherThreads ? tw : kGatherThreads;
-    *chunk_w = (int32_t)cw;
-    *n_chunks = (int32_t)((tw + cw - 1) / cw);
-    int th = (int)((cw + 31) / 32 * 32);
-    *threads = th < 32 ? 32 : th;
-}
+inline int32_t chunks_of(int64_t tw) { return (int32_t)((tw + kChunkW - 1) / kChunkW); }
 
 inline int grid_for(int64_t n_tiles, int num_sms, int ctas_per_sm = kCtasPerSm) {
     const int64_t cap = (int64_t)num_sms * ctas_per_sm;
@@ -254,11 +306,9 @@ inline int grid_for(int64_t n_tiles, int num_sms, int ctas_per_sm = kCtasPerSm) 
 
 cudaError_t launch_gather(const GatherArgs &a, int num_sms, int ctas_per_sm, cudaStream_t s) {
     if (a.n_rows <= 0 || a.tw <= 0) return cudaSuccess;
-    int32_t chunk_w, n_chunks;
-    int threads;
-    chunking(a.tw, &chunk_w, &n_chunks, &threads);
-    k_gather_xor<<<grid_for((int64_t)n_chunks * a.n_rows, num_sms, ctas_per_sm), threads, 0, s>>>(a, chunk_w,
-                                                                                   n_chunks);
+    const int32_t n_chunks = chunks_of(a.tw);
+    k_gather_xor<<<grid_for((int64_t)n_chunks * a.n_rows, num_sms, ctas_per_sm), kGatherThreads, 0, s>>>(
+        a, n_chunks);
     return cudaGetLastError();
 }
 
@@ -298,19 +348,17 @@ cudaError_t launch_update(const fs_code *c, const int32_t *idx, int32_t n_idx, c
     k_update_init<<<grid_for((nb + 255) / 256, c->num_sms), 256, 0, s>>>(a);
     if (n_idx > 0) {
         k_update_mark<<<grid_for((n_idx + 255) / 256, c->num_sms), 256, 0, s>>>(a);
-        int32_t chunk_w, n_chunks;
-        int threads;
-        chunking(c->tw, &chunk_w, &n_chunks, &threads);
+        const int32_t n_chunks = chunks_of(c->tw);
         k_update_delta<<<grid_for((int64_t)n_idx * n_chunks, c->num_sms), kGatherThreads, 0, s>>>(
-            a, chunk_w, n_chunks);
+            a, n_chunks);
         if (c->m > 0) {
             k_update_plist<<<grid_for(c->m, c->num_sms), 128, 0, s>>>(a);
-            k_update_parity<<<grid_for((int64_t)n_chunks * c->m, c->num_sms), threads, 0, s>>>(
-                a, chunk_w, n_chunks);
+            k_update_parity<<<grid_for((int64_t)n_chunks * c->m, c->num_sms), kGatherThreads, 0, s>>>(
+                a, n_chunks);
         }
         if (c->n > 0)
-            k_update_coded<<<grid_for((int64_t)n_chunks * c->n, c->num_sms), threads, 0, s>>>(
-                a, chunk_w, n_chunks);
+            k_update_coded<<<grid_for((int64_t)n_chunks * c->n, c->num_sms), kGatherThreads, 0, s>>>(
+                a, n_chunks);
     }
     return cudaGetLastError();
 }
