@@ -829,8 +829,11 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             const int4 lt = ltab[2 * l];
             const int np = lt.y, ns = lt.w;
             const uint64_t pol_last = l2_policy_last(), pol_first = l2_policy_first();
-            // every (segment, word pair): one gather of at most kRecipeSeg blocks
-            for (int it = threadIdx.x; it < ns * nv; it += blockDim.x) {
+            // every (segment, word pair): one gather of at most kRecipeSeg blocks;
+            // items go to the highest threads first, so the staging above (thread
+            // 0's bulk copies, the low threads' row copies) overlaps them
+            const int rt = (int)blockDim.x - 1 - (int)threadIdx.x;
+            for (int it = rt; it < ns * nv; it += blockDim.x) {
                 const int s = it / nv, k = it - s * nv;
                 const int32_t *rec = pc + (size_t)sp[s] * kRec;
                 const int32_t f = rec[0], g = rec[1], slot = rec[3];
@@ -877,7 +880,7 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
             }
             if (ns > np) {  // some pair has several segments: write their sums
                 __syncthreads();
-                for (int it = threadIdx.x; it < np * lanes; it += blockDim.x) {
+                for (int it = rt; it < np * lanes; it += blockDim.x) {
                     const int q = it / lanes, lane = it - q * lanes;
                     const int32_t *rec = pc + (size_t)q * kRec;
                     const int slot = rec[3];
