@@ -1,16 +1,18 @@
 // fs_encode.cu - encoding (Section 2.2, steps (1) precode and (2) LDGM).
 //
 // k_slices (the default when the code fits): one persistent CTA per SM takes
-// 16-byte byte slices of the stripe from a ticket counter. For a slice it
-// loads that slice of every data block into shared memory with 2-D TMA
-// copies (a box is 16 bytes x up to 256 blocks), computes the m parity
-// slices there (one warp per precode row, lanes splitting the row, a shuffle
-// reduction), then the n coded slices (one lane per coded row; rows sorted
-// by degree into warp groups so the lanes of a warp do equal work, their
-// slot lists column-major so a warp reads its indices in one transaction).
-// Every gathered operand comes from shared memory: each input byte crosses
-// DRAM once and L2 only serves the index tables. Two slice buffers let the
-// TMA copies of the next slice run under the arithmetic of the current one.
+// byte slices of the stripe (16 or 32 bytes of every block) from a ticket
+// counter. For a slice it loads that slice of every data block into
+// shared-memory slots with 2-D TMA copies (a box is 16 or 32 bytes x up to
+// 256 blocks) and computes every output row of the slice from the slots,
+// one lane per row: first the m parity rows together with the coded rows
+// that read no parity, then the coded rows that read one. Rows are packed
+// into warp groups whose quarter warps (8 lanes) always read 8 distinct
+// bank groups (rows chosen so their inputs spread over the groups, each
+// quarter's inputs placed by an edge colouring), with the index tables in
+// shared memory. Every gathered operand comes from shared memory: each
+// input byte crosses DRAM once. Two slot buffers let the TMA copies of the
+// next slice run under the arithmetic of the current one.
 //
 // k_rows (fallback for codes whose slice does not fit) in two launches:
 // first the m precode rows (parities, over the data blocks), then the n LT
@@ -214,13 +216,15 @@ __global__ void __launch_bounds__(kEncThreads, kCtasPerSm) k_rows(RowArgs a) {
 constexpr int kSliceThreads = 1024;
 constexpr long long kSliceWait = 1ll << 22;  // bounded mbarrier waits
 constexpr uint16_t kNoSlot = 0xFFFF;
+constexpr int32_t kPieceMax = 24;  // members of one precode row one lane sums
+constexpr uint32_t kSlotAlign = 256;  // alignment of the slot buffers in shared memory
 
 struct SliceArgs {
     const uint4 *tab;         // tables (copied to shared memory at start)
     int32_t tab_words;        // 16-byte words of tab
-    int32_t off_row, off_pptr, off_pre, off_idx;  // byte offsets inside tab
+    int32_t off_row, off_idx; // byte offsets inside tab
     uint4 *parity, *coded;
-    int32_t m, n_grp, bpad, zbase, slots, box_rows, n_boxes, nbuf;
+    int32_t m, n_grp, n_grp_p, n_grp_a, bpad, zbase, slots, box_rows, n_boxes, nbuf;
     int64_t tw;               // 16-byte words per block
     int32_t n_slices;         // byte slices of the stripe
     int32_t *ticket;          // workspace counter, zero at launch
@@ -284,8 +288,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity) {
 // Views of the tables once they sit in shared memory.
 struct SliceTables {
     const int2 *grp;
-    const uint16_t *grow, *pre, *gidx;
-    const int32_t *pptr;
+    const uint16_t *grow, *gidx;
 };
 
 template <int V>
@@ -294,101 +297,97 @@ __device__ __forceinline__ void gather(uint4 *acc, const uint4 *slot, uint16_t s
     for (int h = 0; h < V; ++h) xor_in(acc[h], slot[unit_of<V>(s, h)]);
 }
 
-// Parity and coded slices of byte slice t from the data slots of `slot`
-// (parity j goes to slot bpad + j). Ends with a barrier.
+// d ^= v in shared memory, fire-and-forget
+__device__ __forceinline__ void red_xor16(uint4 *d, const uint4 &v) {
+    const uint32_t p = saddr(d);
+    asm volatile("red.shared.xor.b32 [%0], %1;\n" ::"r"(p), "r"(v.x) : "memory");
+    asm volatile("red.shared.xor.b32 [%0], %1;\n" ::"r"(p + 4), "r"(v.y) : "memory");
+    asm volatile("red.shared.xor.b32 [%0], %1;\n" ::"r"(p + 8), "r"(v.z) : "memory");
+    asm volatile("red.shared.xor.b32 [%0], %1;\n" ::"r"(p + 12), "r"(v.w) : "memory");
+}
+
+// Zeroes the m parity slots of one slot buffer.
 template <int V>
-__device__ __forceinline__ void compute_slice(const SliceArgs &a, const SliceTables &tb, uint4 *slot,
-                                              int32_t t) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int64_t w0 = (int64_t)t * V;  // first 16-byte word of the slice
-    // step (1): parity slices, one quarter warp (8 lanes) per precode row;
-    // a row's member list is whole octets, each in 8 distinct bank groups
-    const int quarter = lane >> 3, p8 = lane & 7;
-    for (int task = warp; task * 4 < a.m; task += nw) {
-        const int j = task * 4 + quarter;
-        const bool on = j < a.m;
-        const int32_t e0 = on ? tb.pptr[j] : 0;
-        const int n_oct = on ? (tb.pptr[j + 1] - e0) >> 3 : 0;
-        const int n_max = __reduce_max_sync(0xffffffffu, n_oct);
-        uint4 acc[V];
+__device__ __forceinline__ void zero_parities(const SliceArgs &a, uint4 *buf) {
+    for (int i = threadIdx.x; i < a.m * V; i += blockDim.x) buf[(size_t)a.bpad * V + i] = make_uint4(0, 0, 0, 0);
+}
+
+// One warp group: 32 output rows, one per lane (pieces of parity rows in
+// the first n_grp_p groups, coded rows after); column c of the group's entries holds
+// each lane's c-th input slot (padding names a zero slot in a bank group the
+// column leaves free). Indices are fetched a step ahead.
+template <int V>
+__device__ __forceinline__ void row_group(const SliceArgs &a, const SliceTables &tb, uint4 *slot,
+                                          int q, int64_t w0) {
+    const int lane = threadIdx.x & 31;
+    const int2 gq = tb.grp[q];
+    const uint16_t *ix = tb.gidx + gq.x + lane;
+    uint4 acc[V];
 #pragma unroll
-        for (int h = 0; h < V; ++h) acc[h] = make_uint4(0, 0, 0, 0);
-        const uint16_t zs = (uint16_t)(a.zbase + p8);  // a zero slot in this lane's own group
-        int k = 0;
-        for (; k + 2 <= n_max; k += 2) {
-            const uint16_t s0 = k < n_oct ? tb.pre[e0 + 8 * k + p8] : zs;
-            const uint16_t s1 = k + 1 < n_oct ? tb.pre[e0 + 8 * k + 8 + p8] : zs;
-            gather<V>(acc, slot, s0);
-            gather<V>(acc, slot, s1);
-        }
-        if (k < n_max) gather<V>(acc, slot, k < n_oct ? tb.pre[e0 + 8 * k + p8] : zs);
+    for (int h = 0; h < V; ++h) acc[h] = make_uint4(0, 0, 0, 0);
+    const uint16_t z = (uint16_t)(a.zbase + (lane & 7));
+    uint16_t cur[4];
 #pragma unroll
-        for (int h = 0; h < V; ++h) {
+    for (int u = 0; u < 4; ++u) cur[u] = u < gq.y ? ix[u * 32] : z;
+    for (int j = 0; j < gq.y; j += 4) {
+        uint16_t nxt[4];
 #pragma unroll
-            for (int o = 4; o > 0; o >>= 1) {
-                acc[h].x ^= __shfl_xor_sync(0xffffffffu, acc[h].x, o);
-                acc[h].y ^= __shfl_xor_sync(0xffffffffu, acc[h].y, o);
-                acc[h].z ^= __shfl_xor_sync(0xffffffffu, acc[h].z, o);
-                acc[h].w ^= __shfl_xor_sync(0xffffffffu, acc[h].w, o);
-            }
-        }
-        if (on && p8 == 0) {
+        for (int u = 0; u < 4; ++u) nxt[u] = j + 4 + u < gq.y ? ix[(j + 4 + u) * 32] : z;
 #pragma unroll
-            for (int h = 0; h < V; ++h) {
-                slot[unit_of<V>(a.bpad + j, h)] = acc[h];
-                if (w0 + h < a.tw) a.parity[(int64_t)j * a.tw + w0 + h] = acc[h];
-            }
-        }
+        for (int u = 0; u < 4; ++u) gather<V>(acc, slot, cur[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cur[u] = nxt[u];
     }
-    __syncthreads();
-    // step (2): coded slices, one lane per coded row, warp groups of 4 quarters
-    for (int q = warp; q < a.n_grp; q += nw) {
-        const int2 gq = tb.grp[q];
-        const uint16_t *ix = tb.gidx + gq.x + lane;
-        uint4 acc[V];
+    const uint16_t row = tb.grow[q * 32 + lane];
+    if (row == kNoSlot) return;
+    if (q < a.n_grp_p) {  // a piece of a parity row: XOR it into the parity's slot
 #pragma unroll
-        for (int h = 0; h < V; ++h) acc[h] = make_uint4(0, 0, 0, 0);
-        // padding cells name a zero slot in a bank group the column leaves free
-        int j = 0;
-        for (; j + 4 <= gq.y; j += 4) {
-            uint16_t s4[4];
+        for (int h = 0; h < V; ++h) red_xor16(slot + unit_of<V>(a.bpad + row, h), acc[h]);
+    } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) s4[u] = ix[(j + u) * 32];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) gather<V>(acc, slot, s4[u]);
-        }
-        for (; j < gq.y; ++j) gather<V>(acc, slot, ix[j * 32]);
-        const uint16_t row = tb.grow[q * 32 + lane];
-        if (row != kNoSlot) {
-#pragma unroll
-            for (int h = 0; h < V; ++h)
-                if (w0 + h < a.tw) __stcs(a.coded + (int64_t)row * a.tw + w0 + h, acc[h]);
-        }
+        for (int h = 0; h < V; ++h)
+            if (w0 + h < a.tw) __stcs(a.coded + (int64_t)row * a.tw + w0 + h, acc[h]);
     }
-    __syncthreads();  // the slots are free again
+}
+
+// Warps take the n items of a phase from a shared counter (largest first in
+// table order), lane 0 drawing for the warp.
+template <typename Item>
+__device__ __forceinline__ void drain(int *ctr, int n, Item item) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int i = 0;
+        if (lane == 0) i = atomicAdd(ctr, 1);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= n) break;
+        item(i);
+    }
 }
 
 // V 16-byte words per slot (slices of 16 V bytes), data slices by 2-D TMA
-// boxes (one thread issues, an mbarrier completes), nbuf slot buffers.
+// boxes (one thread issues, an mbarrier completes), nbuf slot buffers. A
+// slice takes two phases: the parities together with the coded rows that
+// read no parity, then (after a barrier) the coded rows that read one.
 template <int V>
 __global__ void __launch_bounds__(kSliceThreads, 1)
     k_slices(const __grid_constant__ CUtensorMap map, SliceArgs a) {
-    extern __shared__ __align__(1024) unsigned char s_raw[];
+    extern __shared__ __align__(256) unsigned char s_raw[];
+    // 256-byte aligned slots (the 32B swizzle pattern repeats every 256 bytes);
     // offset from s_raw (not integer casts) so every access stays a shared-space load
-    uint4 *slot0 = reinterpret_cast<uint4 *>(s_raw + ((1024u - (saddr(s_raw) & 1023u)) & 1023u));
+    uint4 *slot0 = reinterpret_cast<uint4 *>(s_raw + ((kSlotAlign - (saddr(s_raw) & (kSlotAlign - 1))) & (kSlotAlign - 1)));
     const size_t buf_words = (size_t)a.slots * V;
     uint4 *s_tab = slot0 + (size_t)a.nbuf * buf_words;
     const unsigned char *tp = reinterpret_cast<const unsigned char *>(s_tab);
     SliceTables tb;
     tb.grp = reinterpret_cast<const int2 *>(tp);
     tb.grow = reinterpret_cast<const uint16_t *>(tp + a.off_row);
-    tb.pptr = reinterpret_cast<const int32_t *>(tp + a.off_pptr);
-    tb.pre = reinterpret_cast<const uint16_t *>(tp + a.off_pre);
     tb.gidx = reinterpret_cast<const uint16_t *>(tp + a.off_idx);
     __shared__ uint64_t s_bar[2];
     __shared__ int32_t s_tk[2];
     __shared__ int32_t s_ok;
+    __shared__ int s_ctr[2];  // work counters of the two phases
     const int32_t n_slices = a.n_slices;
+    const int n_one = a.n_grp_a, n_two = a.n_grp - a.n_grp_a;  // groups of the two phases
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i)
@@ -397,6 +396,8 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         s_tk[0] = atomicAdd(a.ticket, 1);
         if (s_tk[0] < n_slices) issue_slice<V>(&map, a, s_tk[0], slot0, &s_bar[0]);
+        s_ctr[0] = 0;
+        s_ctr[1] = 0;
     }
     // the tables, once per CTA, under the first slice's copies; the zero slots
     for (int32_t i = threadIdx.x; i < a.tab_words; i += blockDim.x) s_tab[i] = __ldg(a.tab + i);
@@ -404,41 +405,58 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
         const int bb = i / (8 * V), r = i % (8 * V);
         if (bb < a.nbuf) slot0[(size_t)bb * buf_words + (size_t)a.zbase * V + r] = make_uint4(0, 0, 0, 0);
     }
+    for (int bb = 0; bb < a.nbuf; ++bb) zero_parities<V>(a, slot0 + (size_t)bb * buf_words);
 
     uint32_t uses0 = 0, uses1 = 0;  // completed phases of each buffer's barrier
     for (int it = 0;; ++it) {
         const int b = a.nbuf == 2 ? (it & 1) : 0;
         uint4 *slot = slot0 + (size_t)b * buf_words;
         if (threadIdx.x == 0) {
-            if (a.nbuf == 2) {  // next slice into the other buffer (free since the last barrier)
+            const int32_t t = s_tk[it & 1];
+            int ok = 1;
+            if (t < n_slices) {
+                ok = wait_phase(&s_bar[b], (b ? uses1 : uses0) & 1) ? 1 : 0;
+                if (!ok) {  // a second bounded wait for the copies in flight, then give up
+                    atomicExch(a.status, (int32_t)FS_ERR_TIMEOUT);
+                    wait_phase(&s_bar[b], (b ? uses1 : uses0) & 1);
+                }
+            }
+            s_ok = ok;
+        }
+        // slice t is in; every warp has left the previous slice (its buffer is free)
+        __syncthreads();
+        const int32_t t = s_tk[it & 1];
+        if (t >= n_slices || !s_ok) break;  // no copies in flight: the next is issued below
+        if (b) ++uses1;
+        else ++uses0;
+        if (threadIdx.x == 0) {
+            s_ctr[1] = 0;
+            if (a.nbuf == 2) {  // next slice into the other buffer
                 const int32_t nx = atomicAdd(a.ticket, 1);
                 s_tk[(it + 1) & 1] = nx;
                 if (nx < n_slices)
                     issue_slice<V>(&map, a, nx, slot0 + (size_t)(b ^ 1) * buf_words, &s_bar[b ^ 1]);
             }
-            const int32_t t = s_tk[it & 1];
-            int ok = 1;
-            if (t < n_slices) {
-                ok = wait_phase(&s_bar[b], (b ? uses1 : uses0) & 1) ? 1 : 0;
-                if (!ok) {
-                    atomicExch(a.status, (int32_t)FS_ERR_TIMEOUT);
-                    // give the other buffer's copies (if any) a bounded time to land
-                    if (a.nbuf == 2 && s_tk[(it + 1) & 1] < n_slices)
-                        wait_phase(&s_bar[b ^ 1], (b ? uses0 : uses1) & 1);
-                }
-            }
-            s_ok = ok;
         }
-        __syncthreads();
-        const int32_t t = s_tk[it & 1];
-        if (t >= n_slices || !s_ok) break;
-        if (b) ++uses1;
-        else ++uses0;
-        compute_slice<V>(a, tb, slot, t);
-        if (a.nbuf == 1 && threadIdx.x == 0) {
-            const int32_t nx = atomicAdd(a.ticket, 1);
-            s_tk[(it + 1) & 1] = nx;
-            if (nx < n_slices) issue_slice<V>(&map, a, nx, slot0, &s_bar[0]);
+        // the other buffer's parity slots (last read by the previous slice) for the next slice
+        if (a.nbuf == 2) zero_parities<V>(a, slot0 + (size_t)(b ^ 1) * buf_words);
+        const int64_t w0 = (int64_t)t * V;  // first 16-byte word of the slice
+        drain(&s_ctr[0], n_one, [&](int i) { row_group<V>(a, tb, slot, i, w0); });
+        __syncthreads();  // the parity slots are complete
+        if (threadIdx.x == 0) s_ctr[0] = 0;
+        for (int i = threadIdx.x; i < a.m * V; i += blockDim.x) {
+            const int j = i / V, h = i - j * V;
+            if (w0 + h < a.tw) a.parity[(int64_t)j * a.tw + w0 + h] = slot[unit_of<V>(a.bpad + j, h)];
+        }
+        drain(&s_ctr[1], n_two, [&](int i) { row_group<V>(a, tb, slot, a.n_grp_a + i, w0); });
+        if (a.nbuf == 1) {
+            __syncthreads();  // the only buffer is free
+            zero_parities<V>(a, slot0);
+            if (threadIdx.x == 0) {
+                const int32_t nx = atomicAdd(a.ticket, 1);
+                s_tk[(it + 1) & 1] = nx;
+                if (nx < n_slices) issue_slice<V>(&map, a, nx, slot0, &s_bar[0]);
+            }
         }
     }
 }
@@ -461,7 +479,7 @@ EncodeTiledFn tensor_map_encoder() {
 
 size_t slice_smem_bytes(const fs_code *c, int v, int nbuf) {
     // slot buffers, tables, alignment slack
-    return (size_t)nbuf * (size_t)c->sl_slots * 16 * v + (size_t)c->sl_tab_bytes + 1024;
+    return (size_t)nbuf * (size_t)c->sl_slots * 16 * v + (size_t)c->sl_tab_bytes + kSlotAlign;
 }
 
 int grid_for(int64_t n_tiles, int num_sms, int ctas_per_sm) {
@@ -530,47 +548,11 @@ std::vector<int> colour_edges(const std::vector<std::pair<int, int>> &edges, int
     return col;
 }
 
-// Orders one precode row's member slots into octets (8 lanes of a quarter
-// warp) that repeat a bank group as little as possible: each octet first
-// takes one member from each group, fullest groups first. The last octet is
-// filled with zero slots (zbase + group) of groups it does not use.
-void pack_octets(std::vector<uint16_t> members, int32_t zbase, std::vector<uint16_t> &out) {
-    std::vector<uint16_t> by[8];
-    for (uint16_t s : members) by[bank_group(s)].push_back(s);
-    size_t left = members.size();
-    while (left) {
-        int taken = 0;
-        while (taken < 8 && left) {
-            int order[8];
-            std::iota(order, order + 8, 0);
-            std::stable_sort(order, order + 8,
-                             [&](int x, int y) { return by[x].size() > by[y].size(); });
-            for (int i = 0; i < 8 && taken < 8; ++i) {
-                std::vector<uint16_t> &l = by[order[i]];
-                if (l.empty()) break;
-                out.push_back(l.back());
-                l.pop_back();
-                ++taken;
-                --left;
-            }
-        }
-        if (taken < 8) {  // last octet: zero slots in the groups it leaves free
-            bool used[8] = {false};
-            for (size_t i = out.size() - taken; i < out.size(); ++i) used[bank_group(out[i])] = true;
-            for (int k = 0; k < 8 && taken < 8; ++k)
-                if (!used[k]) {
-                    out.push_back((uint16_t)(zbase + k));
-                    ++taken;
-                }
-        }
-    }
-}
-
 }  // namespace
 
 cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t *con_idx) {
     c->sl_slots = 0;
-    if (c->b < 1 || c->n < 1 || c->n >= kNoSlot) return cudaSuccess;
+    if (c->b < 1 || c->n < 1 || c->n >= kNoSlot || c->m >= kNoSlot) return cudaSuccess;
     const int32_t box_rows = c->b < 256 ? c->b : 256;
     const int64_t bpad = ((int64_t)c->b + box_rows - 1) / box_rows * box_rows;
     // data slots, parity slots, then 8 zero slots (one per bank group)
@@ -580,59 +562,99 @@ cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t
     auto slot_of = [&](int32_t v) -> uint16_t {
         return (uint16_t)(v < c->b ? v : bpad + (v - c->b));
     };
-    const int32_t n = c->n;
-    auto deg = [&](int32_t r) { return con_ptr[r + 1] - con_ptr[r]; };
+    const int32_t n = c->n, m = c->m;
+    // every output row as a list of slots: the precode rows (members only;
+    // the joint graph's check row n + j ends with its own parity), each cut
+    // into ks pieces of at most kPieceMax members that different lanes sum
+    // (long rows would otherwise hold one warp far longer than the others),
+    // then the n coded rows
+    int32_t max_pre = 0;
+    for (int32_t j = 0; j < m; ++j) max_pre = std::max(max_pre, con_ptr[n + j + 1] - con_ptr[n + j] - 1);
+    const int32_t ks = std::max<int32_t>(1, (max_pre + kPieceMax - 1) / kPieceMax);
+    const int32_t mp = m * ks;  // parity pieces: piece p belongs to parity p / ks
+    if (mp >= kNoSlot) return cudaSuccess;
+    std::vector<std::vector<uint16_t>> in((size_t)mp + n);
+    for (int32_t j = 0; j < m; ++j) {
+        const int32_t e0 = con_ptr[n + j], len = con_ptr[n + j + 1] - 1 - e0;
+        for (int32_t k = 0; k < ks; ++k)
+            for (int32_t e = e0 + (int32_t)((int64_t)len * k / ks); e < e0 + (int32_t)((int64_t)len * (k + 1) / ks); ++e)
+                in[(size_t)j * ks + k].push_back(slot_of(con_idx[e]));
+    }
+    for (int32_t r = 0; r < n; ++r)
+        for (int32_t e = con_ptr[r]; e < con_ptr[r + 1]; ++e) in[(size_t)mp + r].push_back(slot_of(con_idx[e]));
+    auto deg = [&](int32_t id) { return (int)in[id].size(); };
 
-    // coded rows into quarters of 8: rows of about the same degree (largest
-    // first) whose neighbours spread evenly over the bank groups
-    std::vector<int32_t> order(n);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return deg(x) > deg(y); });
-    std::vector<char> used(n, 0);
+    // rows into quarters of 8 (rows of about the same length, largest first,
+    // whose inputs spread evenly over the bank groups), quarters sorted by
+    // width and padded to whole warp groups
     struct Quarter {
         int32_t row[8];
         int delta;
     };
     std::vector<Quarter> quarters;
-    constexpr int kWindow = 64;  // candidates looked at for each place
-    size_t pos = 0;
-    for (;;) {
-        while (pos < (size_t)n && used[order[pos]]) ++pos;
-        if (pos >= (size_t)n) break;
-        Quarter q;
-        std::fill(q.row, q.row + 8, -1);
-        int cnt[8] = {0};
-        int dmax = deg(order[pos]);
-        for (int k = 0; k < 8; ++k) {
-            int32_t best = -1;
-            int best_key = 0, best_deg = 0;
-            int seen = 0;
-            for (size_t i = pos; i < (size_t)n && seen < (k == 0 ? 1 : kWindow); ++i) {
-                const int32_t r = order[i];
-                if (used[r]) continue;
-                ++seen;
-                int c2[8];
-                std::copy(cnt, cnt + 8, c2);
-                for (int32_t e = con_ptr[r]; e < con_ptr[r + 1]; ++e) ++c2[bank_group(slot_of(con_idx[e]))];
-                const int key = std::max(*std::max_element(c2, c2 + 8), dmax);
-                if (best < 0 || key < best_key || (key == best_key && deg(r) > best_deg)) {
-                    best = r;
-                    best_key = key;
-                    best_deg = deg(r);
+    std::vector<char> used((size_t)mp + n, 0);
+    auto build_quarters = [&](std::vector<int32_t> order) {
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return deg(x) > deg(y); });
+        std::vector<Quarter> qs;
+        constexpr int kWindow = 64;  // candidates looked at for each place
+        size_t pos = 0;
+        for (;;) {
+            while (pos < order.size() && used[order[pos]]) ++pos;
+            if (pos >= order.size()) break;
+            Quarter q;
+            std::fill(q.row, q.row + 8, -1);
+            int cnt[8] = {0};
+            const int dmax = deg(order[pos]);
+            for (int k = 0; k < 8; ++k) {
+                int32_t best = -1;
+                int best_key = 0, best_deg = 0;
+                int seen = 0;
+                for (size_t i = pos; i < order.size() && seen < (k == 0 ? 1 : kWindow); ++i) {
+                    const int32_t r = order[i];
+                    if (used[r]) continue;
+                    ++seen;
+                    int c2[8];
+                    std::copy(cnt, cnt + 8, c2);
+                    for (uint16_t sl : in[r]) ++c2[bank_group(sl)];
+                    const int key = std::max(*std::max_element(c2, c2 + 8), dmax);
+                    if (best < 0 || key < best_key || (key == best_key && deg(r) > best_deg)) {
+                        best = r;
+                        best_key = key;
+                        best_deg = deg(r);
+                    }
                 }
+                if (best < 0) break;
+                used[best] = 1;
+                q.row[k] = best;
+                for (uint16_t sl : in[best]) ++cnt[bank_group(sl)];
             }
-            if (best < 0) break;
-            used[best] = 1;
-            q.row[k] = best;
-            for (int32_t e = con_ptr[best]; e < con_ptr[best + 1]; ++e)
-                ++cnt[bank_group(slot_of(con_idx[e]))];
+            q.delta = std::max(*std::max_element(cnt, cnt + 8), dmax);
+            qs.push_back(q);
         }
-        q.delta = std::max(*std::max_element(cnt, cnt + 8), dmax);
-        quarters.push_back(q);
+        std::stable_sort(qs.begin(), qs.end(), [](const Quarter &x, const Quarter &y) { return x.delta > y.delta; });
+        while (qs.size() % 4) {  // empty quarters complete the last warp group
+            Quarter e;
+            std::fill(e.row, e.row + 8, -1);
+            e.delta = 0;
+            qs.push_back(e);
+        }
+        quarters.insert(quarters.end(), qs.begin(), qs.end());
+    };
+    // parity rows; coded rows that read no parity (computed beside the
+    // parities); coded rows that read one (after them)
+    std::vector<int32_t> set_p, set_a, set_b;
+    for (int32_t p = 0; p < mp; ++p) set_p.push_back(p);
+    for (int32_t r = 0; r < n; ++r) {
+        bool par = false;
+        for (int32_t e = con_ptr[r]; e < con_ptr[r + 1]; ++e) par |= con_idx[e] >= c->b;
+        (par ? set_b : set_a).push_back(mp + r);
     }
-    std::stable_sort(quarters.begin(), quarters.end(),
-                     [](const Quarter &x, const Quarter &y) { return x.delta > y.delta; });
-    const int32_t n_grp = (int32_t)((quarters.size() + 3) / 4);
+    build_quarters(set_p);
+    const int32_t n_grp_p = (int32_t)(quarters.size() / 4);
+    build_quarters(set_a);
+    const int32_t n_grp_a = (int32_t)(quarters.size() / 4);
+    build_quarters(set_b);
+    const int32_t n_grp = (int32_t)(quarters.size() / 4);
     std::vector<int2> grp(n_grp);
     int64_t total = 0;
     for (int32_t gq = 0; gq < n_grp; ++gq) {
@@ -641,36 +663,19 @@ cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t
         total += 32 * (int64_t)cols;
         if (total > (int64_t)1 << 24) return cudaSuccess;
     }
-    // precode rows: members (the joint graph's check rows end with their own
-    // parity, left out) packed into octets
-    std::vector<int32_t> pptr((size_t)c->m + 1, 0);
-    std::vector<uint16_t> pre;
-    for (int32_t j = 0; j < c->m; ++j) {
-        const int32_t g = n + j;
-        std::vector<uint16_t> mem;
-        for (int32_t e = con_ptr[g]; e < con_ptr[g + 1] - 1; ++e) mem.push_back(slot_of(con_idx[e]));
-        pack_octets(std::move(mem), (int32_t)zbase, pre);
-        pptr[j + 1] = (int32_t)pre.size();
-    }
 
     auto al16 = [](int64_t x) { return (x + 15) & ~(int64_t)15; };
     const int64_t off_row = al16((int64_t)sizeof(int2) * n_grp);
-    const int64_t off_pptr = al16(off_row + 2 * 32 * (int64_t)n_grp);
-    const int64_t off_pre = al16(off_pptr + 4 * ((int64_t)c->m + 1));
-    const int64_t off_idx = al16(off_pre + 2 * (int64_t)pre.size());
+    const int64_t off_idx = al16(off_row + 2 * 32 * (int64_t)n_grp);
     const int64_t bytes = al16(off_idx + 2 * total);
-    if ((size_t)slots * 16 + (size_t)bytes + 1024 > c->smem_optin) return cudaSuccess;
+    if ((size_t)slots * 16 + (size_t)bytes + kSlotAlign > c->smem_optin) return cudaSuccess;
 
     std::vector<unsigned char> tab((size_t)bytes, 0);
     memcpy(tab.data(), grp.data(), sizeof(int2) * n_grp);
     uint16_t *row = reinterpret_cast<uint16_t *>(tab.data() + off_row);
-    int32_t *tp = reinterpret_cast<int32_t *>(tab.data() + off_pptr);
-    uint16_t *tpre = reinterpret_cast<uint16_t *>(tab.data() + off_pre);
     uint16_t *idx = reinterpret_cast<uint16_t *>(tab.data() + off_idx);
     std::fill(row, row + 32 * (size_t)n_grp, kNoSlot);
     std::fill(idx, idx + total, kNoSlot);
-    std::copy(pptr.begin(), pptr.end(), tp);
-    std::copy(pre.begin(), pre.end(), tpre);
     std::vector<std::pair<int, int>> edges;
     std::vector<uint16_t> eslot;
     for (size_t qi = 0; qi < quarters.size(); ++qi) {
@@ -680,9 +685,9 @@ cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t
         eslot.clear();
         for (int p = 0; p < 8; ++p) {
             if (q.row[p] < 0) continue;
-            row[(size_t)gq * 32 + lane0 + p] = (uint16_t)q.row[p];
-            for (int32_t e = con_ptr[q.row[p]]; e < con_ptr[q.row[p] + 1]; ++e) {
-                const uint16_t sl = slot_of(con_idx[e]);
+            // output id: the parity index, or the coded row
+            row[(size_t)gq * 32 + lane0 + p] = (uint16_t)(q.row[p] < mp ? q.row[p] / ks : q.row[p] - mp);
+            for (uint16_t sl : in[q.row[p]]) {
                 edges.emplace_back(p, bank_group(sl));
                 eslot.push_back(sl);
             }
@@ -693,22 +698,17 @@ cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t
         // empty cells of each column: the zero slot of a group the column leaves free
         for (int cc = 0; cc < grp[gq].y; ++cc) {
             uint16_t *cell = idx + (size_t)grp[gq].x + (size_t)cc * 32 + lane0;
-            bool used[8] = {false};
+            bool taken[8] = {false};
             for (int p = 0; p < 8; ++p)
-                if (cell[p] != kNoSlot) used[bank_group(cell[p])] = true;
+                if (cell[p] != kNoSlot) taken[bank_group(cell[p])] = true;
             int k = 0;
             for (int p = 0; p < 8; ++p) {
                 if (cell[p] != kNoSlot) continue;
-                while (k < 7 && used[k]) ++k;
+                while (k < 7 && taken[k]) ++k;
                 cell[p] = (uint16_t)(zbase + k);
             }
         }
     }
-    // quarters of the last group that hold no rows
-    for (size_t qi = quarters.size(); qi < 4 * (size_t)n_grp; ++qi)
-        for (int cc = 0; cc < grp[qi / 4].y; ++cc)
-            for (int p = 0; p < 8; ++p)
-                idx[(size_t)grp[qi / 4].x + (size_t)cc * 32 + 8 * (qi % 4) + p] = (uint16_t)(zbase + p);
 
     cudaError_t e = cudaMalloc(&c->sl_tab, (size_t)bytes);
     if (e == cudaSuccess) e = cudaMemcpy(c->sl_tab, tab.data(), (size_t)bytes, cudaMemcpyHostToDevice);
@@ -716,10 +716,10 @@ cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t
     c->sl_box_rows = box_rows;
     c->sl_bpad = (int32_t)bpad;
     c->sl_n_grp = n_grp;
+    c->sl_n_grp_p = n_grp_p;
+    c->sl_n_grp_a = n_grp_a;
     c->sl_tab_bytes = (int32_t)bytes;
     c->sl_off_row = (int32_t)off_row;
-    c->sl_off_pptr = (int32_t)off_pptr;
-    c->sl_off_pre = (int32_t)off_pre;
     c->sl_off_idx = (int32_t)off_idx;
     c->sl_zbase = (int32_t)zbase;
     c->sl_slots = (int32_t)slots;
@@ -761,13 +761,13 @@ bool launch_slices(const fs_code *c, const void *data, void *parity, void *coded
     a.tab = reinterpret_cast<const uint4 *>(c->sl_tab);
     a.tab_words = c->sl_tab_bytes / 16;
     a.off_row = c->sl_off_row;
-    a.off_pptr = c->sl_off_pptr;
-    a.off_pre = c->sl_off_pre;
     a.off_idx = c->sl_off_idx;
     a.parity = static_cast<uint4 *>(parity);
     a.coded = static_cast<uint4 *>(coded);
     a.m = c->m;
     a.n_grp = c->sl_n_grp;
+    a.n_grp_p = c->sl_n_grp_p;
+    a.n_grp_a = c->sl_n_grp_a;
     a.bpad = c->sl_bpad;
     a.zbase = c->sl_zbase;
     a.slots = c->sl_slots;

@@ -48,17 +48,18 @@ struct fs_code {
     int32_t sl_bpad;      // data slots, b rounded up to sl_box_rows
     int32_t sl_zbase;     // first of 8 zero slots (one per bank group), after the parities
     int32_t sl_slots;     // slots of one buffer (sl_zbase + 8)
-    int32_t sl_n_grp;     // warp groups of 32 coded rows, by degree
+    int32_t sl_n_grp;     // warp groups of 32 output rows
+    int32_t sl_n_grp_p;   // the first sl_n_grp_p groups are precode (parity) rows,
+    int32_t sl_n_grp_a;   // groups up to sl_n_grp_a coded rows that read no parity
     // one device array holding the tables the kernel copies to shared
     // memory, each part starting on a 16-byte boundary:
-    //   grp   int2 [sl_n_grp]       {first entry, degree of the group}
-    //   row   uint16 [32 sl_n_grp]  coded row of each lane, 0xFFFF pad
-    //   pptr  int32 [m + 1]         precode row starts
-    //   pre   uint16 [e_pre]        precode members as slots
-    //   idx   uint16 [...]          group entries, column-major, 0xFFFF pad
+    //   grp   int2 [sl_n_grp]       {first entry, columns of the group}
+    //   row   uint16 [32 sl_n_grp]  output row of each lane (parity index or
+    //                               coded row), 0xFFFF pad
+    //   idx   uint16 [...]          group entries, column-major (32 lanes)
     unsigned char *sl_tab;
     int32_t sl_tab_bytes;  // multiple of 16
-    int32_t sl_off_row, sl_off_pptr, sl_off_pre, sl_off_idx;  // byte offsets
+    int32_t sl_off_row, sl_off_idx;  // byte offsets
 };
 
 // Builds the slice encode tables of c (host arrays of the joint graph);
