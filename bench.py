@@ -40,6 +40,12 @@ from paper_1702_07409_gb300 import gen  # noqa: E402
 B, M, N_CODED, T = 4096, 128, 5400, 65536
 ERASE_FRAC, UPDATE_FRAC, REPAIR_FRAC = 0.20, 0.01, 0.05
 METRIC = "encode & BP-decode source GB/s"
+# DRAM bytes (read + write) of one launch at this workload, from the ncu
+# captures summarised in profiles/k_peel_precoded_k4096_t64k.md and
+# profiles/k_slices_precoded_k4096_t64k.md (valid while those kernels are
+# unchanged)
+PEEL_TRAFFIC_BYTES = 1038658000 + 277923072
+SLICES_TRAFFIC_BYTES = 273326080 + 313617408
 WORKLOAD = ("precoded LDGM stripe: b=4096 x 64 KiB data, m=128 checks (3 per data block), "
             "n=5400, FiniteDist max-degree-40, 20% erasures; step = encode + decode + "
             "1% update + 5% repair")
@@ -305,10 +311,9 @@ def run_gpu(args):
     gbs = world * src_bytes / (ms_step * 1e-3) / 1e9
     gbs_e2e = world * src_bytes / (ms_e2e * 1e-3) / 1e9
 
-    # roofline of the encode launches: algorithmic bytes = data read once,
-    # parities written, coded blocks written
-    enc_bytes = (B + M + N_CODED) * T
-    enc_gbs = enc_bytes / (op_ms["encode"] * 1e-3) / 1e9
+    # roofline of the kernel with the largest share of the step: the payload
+    # peel (k_peel). Algorithmic bytes = the coded payloads of the pairs whose
+    # constraint is a coded row (read) + the recovered data blocks (written).
     g = st.g
     dec_pairs_lt = None
     try:
@@ -319,6 +324,9 @@ def run_gpu(args):
         pass
     dec_bytes = ((dec_pairs_lt or 0) + (B - unrec_data)) * T
     dec_gbs = dec_bytes / (op_ms["decode_payload"] * 1e-3) / 1e9
+    # encode (k_slices): data read once, parities and coded blocks written once
+    enc_bytes = (B + M + N_CODED) * T
+    enc_gbs = enc_bytes / (op_ms["encode"] * 1e-3) / 1e9
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": world,
@@ -336,12 +344,16 @@ def run_gpu(args):
         "encode_source_gbs": round(B * T / (op_ms["encode"] * 1e-3) / 1e9, 1),
         "decode_source_gbs": round(recovered / ((op_ms["decode_schedule"] +
                                                   op_ms["decode_payload"]) * 1e-3) / 1e9, 1),
-        "roofline": {"bound": "hbm", "kernel": "fs_encode (precode + LT gather launches)",
-                     "achieved": round(enc_gbs, 1), "peak": peak, "peak_kind": peak_kind,
-                     "unit": "GB/s", "frac": round(enc_gbs / peak, 4), "traffic": None,
-                     "algorithmic_bytes": enc_bytes},
-        "decode_payload_roofline": {"achieved": round(dec_gbs, 1), "frac": round(dec_gbs / peak, 4),
-                                    "algorithmic_bytes": dec_bytes},
+        "roofline": {"bound": "hbm", "kernel": "k_peel (fs_decode_payload)",
+                     "achieved": round(dec_gbs, 1), "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s", "frac": round(dec_gbs / peak, 4),
+                     "traffic": PEEL_TRAFFIC_BYTES if T == 65536 else None,
+                     "algorithmic_bytes": dec_bytes},
+        "encode_roofline": {"bound": "hbm", "kernel": "k_slices (fs_encode)",
+                            "achieved": round(enc_gbs, 1), "peak": peak, "unit": "GB/s",
+                            "frac": round(enc_gbs / peak, 4),
+                            "traffic": SLICES_TRAFFIC_BYTES if T == 65536 else None,
+                            "algorithmic_bytes": enc_bytes},
         "e2e": {"value": round(gbs_e2e, 2), "unit": "GB/s", "ms_per_step": round(ms_e2e, 4),
                 "h2d_bytes_per_step": st.h2d_bytes(), "d2h_bytes_per_step": st.d2h_bytes()},
         "gpu_launches": Stripe.LAUNCHES_PER_STEP * K,

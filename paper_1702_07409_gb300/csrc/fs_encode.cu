@@ -781,7 +781,11 @@ bool launch_slices(const fs_code *c, const void *data, void *parity, void *coded
     auto kern = v == 2 ? k_slices<2> : k_slices<1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-        const int64_t g = a.n_slices < c->num_sms ? a.n_slices : c->num_sms;
+        // one CTA per SM but one: each CTA fills its SM's shared memory, so a
+        // one-CTA decoding schedule launched beside the encode on another
+        // stream would otherwise wait for the whole encode
+        const int64_t sms = c->num_sms > 1 ? c->num_sms - 1 : 1;
+        const int64_t g = a.n_slices < sms ? a.n_slices : sms;
         kern<<<(int)(g < 1 ? 1 : g), kSliceThreads, smem, s>>>(map, a);
         e = cudaGetLastError();
     }
