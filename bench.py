@@ -153,17 +153,25 @@ class Stripe:
                 self.code.set_tuning(knob, value)
         host = gen.fill_bytes(gen.SEED_DATA + off, B * T).reshape(B, T)
         self.host_data = torch.from_numpy(host).pin_memory()
-        self.d = self.host_data.to(device)
         self.p = torch.empty((M, T), dtype=torch.uint8, device=device)
         self.cd = torch.empty((N_CODED, T), dtype=torch.uint8, device=device)
-        self.out = torch.empty((B, T), dtype=torch.uint8, device=device)
-        self.unrec = torch.empty(B + M, dtype=torch.uint8, device=device)
-        self.nun = torch.empty(1, dtype=torch.int32, device=device)
         er = np.zeros(N_CODED, np.uint8)
         er[gen.sample_indices(N_CODED, gen.round_count(ERASE_FRAC, N_CODED),
                               gen.SEED_ERASE + off)] = 1
         self.host_erased = torch.from_numpy(er).pin_memory()
-        self.erased = self.host_erased.to(device)
+        # two sets of per-step inputs and outputs: the end-to-end loop uploads
+        # step i+1 and reads back step i-1 while step i computes
+        self.bufs = []
+        for _ in range(2):
+            self.bufs.append({
+                "d": self.host_data.to(device),
+                "erased": self.host_erased.to(device),
+                "out": torch.empty((B, T), dtype=torch.uint8, device=device),
+                "unrec": torch.empty(B + M, dtype=torch.uint8, device=device),
+                "nun": torch.empty(1, dtype=torch.int32, device=device),
+            })
+        self.s_in = torch.cuda.Stream(device=device)
+        self.s_out = torch.cuda.Stream(device=device)
         self.u = gen.round_count(UPDATE_FRAC, B)
         self.nl = gen.round_count(REPAIR_FRAC, N_CODED)
         self.n_rounds = n_rounds
@@ -192,49 +200,83 @@ class Stripe:
     # kernel; decode 2: schedule + payload; update 6; repair 1)
     LAUNCHES_PER_STEP = 10
 
-    def step(self, r: int, ev=None):
-        """encode, decode (schedule + payload), update, repair. The decoding
-        schedule needs only the erasure flags, so with overlap on it runs on a
-        side stream beside the encode (the payload waits for both)."""
+    @property
+    def nun(self):
+        return self.bufs[0]["nun"]
+
+    @property
+    def unrec(self):
+        return self.bufs[0]["unrec"]
+
+    def step(self, r: int, ev=None, k: int = 0):
+        """encode, decode (schedule + payload), update, repair on input set k.
+        The decoding schedule needs only the erasure flags, so with overlap on
+        it runs on a side stream beside the encode (the payload waits for
+        both)."""
         import torch
         c = self.code
+        bk = self.bufs[k]
         r %= self.n_rounds
         main = torch.cuda.current_stream()
         if self.overlap:
             self.side.wait_stream(main)
             with torch.cuda.stream(self.side):
                 if ev: ev[6].record()
-                c.decode_schedule(self.erased, self.unrec, self.nun, self.ws_d)
+                c.decode_schedule(bk["erased"], bk["unrec"], bk["nun"], self.ws_d)
                 if ev: ev[7].record()
         if ev: ev[0].record()
-        c.encode(self.d, self.p, self.cd, self.ws_e)
+        c.encode(bk["d"], self.p, self.cd, self.ws_e)
         if ev: ev[1].record()
         if self.overlap:
             main.wait_stream(self.side)
         else:
             if ev: ev[6].record()
-            c.decode_schedule(self.erased, self.unrec, self.nun, self.ws_d)
+            c.decode_schedule(bk["erased"], bk["unrec"], bk["nun"], self.ws_d)
             if ev: ev[7].record()
         if ev: ev[2].record()
-        c.decode_payload(self.cd, self.out, self.ws_d)
+        c.decode_payload(self.cd, bk["out"], self.ws_d)
         if ev: ev[3].record()
-        c.update(self.idx[r], self.u, self.new[r], self.d, self.p, self.cd, self.ws_u)
+        c.update(self.idx[r], self.u, self.new[r], bk["d"], self.p, self.cd, self.ws_u)
         if ev: ev[4].record()
-        c.repair(self.lost[r], self.nl, self.d, self.p, self.cd, self.ws_r)
+        c.repair(self.lost[r], self.nl, bk["d"], self.p, self.cd, self.ws_r)
         if ev: ev[5].record()
 
-    def step_e2e(self, r: int):
-        """The same step from pinned host buffers: inputs copied in, the
-        decoded data and the unrecovered count copied back."""
-        r %= self.n_rounds
-        self.d.copy_(self.host_data, non_blocking=True)
-        self.erased.copy_(self.host_erased, non_blocking=True)
-        self.idx[r].copy_(self.host_idx[r], non_blocking=True)
-        self.new[r].copy_(self.host_new[r], non_blocking=True)
-        self.lost[r].copy_(self.host_lost[r], non_blocking=True)
-        self.step(r)
-        self.host_out.copy_(self.out, non_blocking=True)
-        self.host_nun.copy_(self.nun, non_blocking=True)
+    def run_e2e(self, rounds):
+        """The steps of `rounds` from pinned host buffers: each step's inputs
+        are copied in and its decoded data and unrecovered count copied back.
+        Uploads run on one copy stream, read-backs on another, so step i+1's
+        upload and step i-1's read-back overlap step i's kernels (input sets
+        alternate)."""
+        import torch
+        main = torch.cuda.current_stream()
+        n = len(rounds)
+        in_done = [torch.cuda.Event() for _ in range(n)]
+        comp_done = [torch.cuda.Event() for _ in range(n)]
+        out_done = [torch.cuda.Event() for _ in range(n)]
+        for i, r in enumerate(rounds):
+            k = i & 1
+            bk = self.bufs[k]
+            r %= self.n_rounds
+            with torch.cuda.stream(self.s_in):
+                if i >= 2:  # input set k is free once step i-2's kernels are done
+                    self.s_in.wait_event(comp_done[i - 2])
+                bk["d"].copy_(self.host_data, non_blocking=True)
+                bk["erased"].copy_(self.host_erased, non_blocking=True)
+                self.idx[r].copy_(self.host_idx[r], non_blocking=True)
+                self.new[r].copy_(self.host_new[r], non_blocking=True)
+                self.lost[r].copy_(self.host_lost[r], non_blocking=True)
+                in_done[i].record(self.s_in)
+            main.wait_event(in_done[i])
+            if i >= 2:  # output set k has been read back
+                main.wait_event(out_done[i - 2])
+            self.step(r, k=k)
+            comp_done[i].record(main)
+            with torch.cuda.stream(self.s_out):
+                self.s_out.wait_event(comp_done[i])
+                self.host_out.copy_(bk["out"], non_blocking=True)
+                self.host_nun.copy_(bk["nun"], non_blocking=True)
+                out_done[i].record(self.s_out)
+        main.wait_stream(self.s_out)
 
     def h2d_bytes(self):
         return B * T + N_CODED + self.u * 4 + self.u * T + self.nl * 4
@@ -293,19 +335,21 @@ def run_gpu(args):
              for o, (a, b) in spans.items()}
 
     # e2e: the same steps from pinned host memory, copies inside the timed region
-    for r in range(min(args.warmup, 2)):
-        st.step_e2e(r)
+    st.run_e2e(list(range(min(args.warmup, 3))))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
     e0.record()
-    for i in range(K):
-        st.step_e2e(args.warmup + i)
+    st.run_e2e([args.warmup + i for i in range(K)])
     e1.record()
     torch.cuda.synchronize()
     barrier()
     ms_e2e = reduce_max(e0.elapsed_time(e1), device) / K
+    # the last step's read-back: the decoded data equal the uploaded data
+    e2e_ok = bool(torch.equal(st.host_out, st.host_data)) if n_unrec == 0 else None
+    if e2e_ok is False:
+        raise RuntimeError("end-to-end read-back differs from the uploaded data")
 
     src_bytes = B * T + recovered
     gbs = world * src_bytes / (ms_step * 1e-3) / 1e9
@@ -334,7 +378,7 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded splitmix64 bytes and graphs)",
         "config": {"workload": WORKLOAD, "b": B, "m": M, "n": N_CODED, "block_bytes": T,
-                   "e_lt": g.e_lt, "e_pre": g.e_pre, "erased": int(st.erased.sum().item()),
+                   "e_lt": g.e_lt, "e_pre": g.e_pre, "erased": int(st.host_erased.sum().item()),
                    "unrecovered": n_unrec, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "schedule_beside_encode": not args.serial_schedule,
@@ -355,7 +399,10 @@ def run_gpu(args):
                             "traffic": SLICES_TRAFFIC_BYTES if T == 65536 else None,
                             "algorithmic_bytes": enc_bytes},
         "e2e": {"value": round(gbs_e2e, 2), "unit": "GB/s", "ms_per_step": round(ms_e2e, 4),
-                "h2d_bytes_per_step": st.h2d_bytes(), "d2h_bytes_per_step": st.d2h_bytes()},
+                "h2d_bytes_per_step": st.h2d_bytes(), "d2h_bytes_per_step": st.d2h_bytes(),
+                "copies": "uploads and read-backs on two copy streams, overlapping the "
+                          "neighbouring steps' kernels (two input sets)",
+                "readback_verified": e2e_ok},
         "gpu_launches": Stripe.LAUNCHES_PER_STEP * K,
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                    "reasons": clocks["reasons"]},
