@@ -250,6 +250,56 @@ fs_status fs_repair(const fs_code *code, const int32_t *d_lost, int32_t n_lost, 
 fs_status fs_encode_static(const fs_code *code, const void *d_data, void *d_parity, void *d_coded,
                            int32_t *d_status, void *stream);
 
+/* ---- batches of stripes --------------------------------------------------
+ * Section 2.2 cuts the data into stripes (b blocks each) that are coded and
+ * decoded independently; a batch runs many stripes, of any sizes and codes,
+ * in a fixed number of launches (encode: one launch for every stripe's
+ * precode rows, one for every stripe's LT rows; decode: one launch of the
+ * symbolic pass, one CTA per stripe, per form, then one launch of the
+ * payload over every (stripe, byte slice)). Each stripe's result is exactly
+ * that of fs_encode / fs_decode on the same arguments.
+ *
+ * A stripe of a batch (host struct; the pointers are device pointers with
+ * the same meaning, layout and alignment rules as the single calls):
+ *   code             the stripe's code (every stripe of a batch on the
+ *                    current device)
+ *   encode: d_data (b·t in), d_parity (m·t out, NULL when m == 0),
+ *           d_coded (n·t out)
+ *   decode: d_coded (n·t in), d_erased (n flags), d_data_out (b·t out),
+ *           d_unrecovered (k_int flags out), d_n_unrecovered (int32 out),
+ *           d_ws (this stripe's fs_workspace_bytes(code, FS_OP_DECODE, 0)
+ *           bytes, 16-byte aligned; after the run it holds the stripe's
+ *           decoding path and status word like after fs_decode)
+ * Unused fields are ignored. */
+typedef struct {
+    const fs_code *code;
+    const void *d_data;
+    void *d_parity;
+    void *d_coded;
+    const uint8_t *d_erased;
+    void *d_data_out;
+    uint8_t *d_unrecovered;
+    int32_t *d_n_unrecovered;
+    void *d_ws;
+} fs_stripe;
+
+typedef struct fs_batch fs_batch; /* opaque; owned by the library */
+
+/* Plans a batch of n stripes for op (FS_OP_ENCODE or FS_OP_DECODE): checks
+ * every stripe (FS_ERR_INVALID on the first bad one, nothing created),
+ * copies the per-stripe launch arguments to device memory (this call
+ * allocates; the run does not). The stripes' buffers and codes must outlive
+ * the batch. Blocks the host; not for stream capture. */
+fs_status fs_batch_create(const fs_stripe *stripes, int32_t n, int op, fs_batch **out);
+
+/* Enqueues the batch on stream (asynchronous, allocates nothing, no host
+ * synchronisation: a run can be captured in a CUDA graph and the graph
+ * replayed). FS_ERR_INVALID when the current device is not the batch's. */
+fs_status fs_batch_run(const fs_batch *batch, void *stream);
+
+/* Waits for the device, then frees the batch's device arrays. */
+void fs_batch_destroy(fs_batch *batch);
+
 /* Static string naming a status. */
 const char *fs_status_string(fs_status s);
 

@@ -51,6 +51,10 @@ constexpr int kRows = 16;                     // rows per ticket
 constexpr int kStage = 2048;                  // neighbour entries of one ticket staged
 constexpr int kCtasPerSm = 5;
 
+}  // namespace
+
+// One job of the row kernel: the rows of one CSR (one stripe's precode or
+// LT rows) over its inputs; a launch runs one job or a batch of them.
 struct RowArgs {
     const int32_t *ptr, *idx;  // CSR rows
     const uint4 *inA, *inB;    // input block v: inA + v*tw (v < split), else inB
@@ -62,8 +66,10 @@ struct RowArgs {
     int stream_out;       // 1: evict-first stores
     int32_t rows;         // rows per ticket (at most kRows)
     int hints;            // 1: inputs evict-last, outputs evict-first in L2
-    int32_t *ticket_ctr;  // workspace counter, zero at launch
+    int32_t t0;           // first ticket of this job in the launch's ticket order
 };
+
+namespace {
 
 __device__ __forceinline__ void xor4(uint4 &a, const uint4 &b) {
     a.x ^= b.x;
@@ -112,53 +118,80 @@ __device__ __forceinline__ void store_row(const RowArgs &a, int32_t row, int64_t
     }
 }
 
-__global__ void __launch_bounds__(kEncThreads, kCtasPerSm) k_rows(RowArgs a) {
+// job of global ticket t: the last job whose first ticket is <= t
+__device__ __forceinline__ int find_job(const RowArgs *jobs, int n_jobs, int32_t t) {
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].t0 <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Tickets run job by job (a stripe's chunks one after the other), so the
+// resident CTAs work on one stripe's byte range at a time.
+__device__ __forceinline__ void rows_body(const RowArgs *jobs, int n_jobs, int32_t n_tickets,
+                                          int32_t *ticket_ctr) {
     // ring of 3 pointer stages (two tickets ahead), 2 neighbour stages, 4 tickets
     __shared__ int32_t s_ptr[3][kRows + 1];
     __shared__ int32_t s_idx[2][kStage];
-    __shared__ int32_t s_tk[4];
-    const int32_t batches = (a.n_rows + a.rows - 1) / a.rows;
-    const int32_t n_tickets = a.n_chunks * batches;
+    __shared__ int32_t s_tk[4], s_jb[4];
 
-    auto stage_ptr = [&](int32_t t, int slot) {
-        if (t >= n_tickets) return;
-        const Ticket k = ticket_of(a, t, batches);
-        for (int i = threadIdx.x; i <= k.nr; i += blockDim.x)
-            cp_async4(&s_ptr[slot][i], a.ptr + k.r0 + i);
+    auto take = [&](int slot, int32_t t) {  // thread 0: ticket t and its job into a slot
+        s_tk[slot] = t;
+        s_jb[slot] = t < n_tickets ? find_job(jobs, n_jobs, t) : 0;
     };
-    auto stage_idx = [&](int32_t t, int pslot, int islot) {
+    auto stage_ptr = [&](int k, int slot) {
+        const int32_t t = s_tk[k];
         if (t >= n_tickets) return;
+        const RowArgs &a = jobs[s_jb[k]];
+        const int32_t batches = (a.n_rows + a.rows - 1) / a.rows;
+        const Ticket tk = ticket_of(a, t - a.t0, batches);
+        for (int i = threadIdx.x; i <= tk.nr; i += blockDim.x)
+            cp_async4(&s_ptr[slot][i], a.ptr + tk.r0 + i);
+    };
+    auto stage_idx = [&](int k, int pslot, int islot) {
+        const int32_t t = s_tk[k];
+        if (t >= n_tickets) return;
+        const RowArgs &a = jobs[s_jb[k]];
+        const int32_t batches = (a.n_rows + a.rows - 1) / a.rows;
         const int32_t e0 = s_ptr[pslot][0];
-        const int32_t ne = s_ptr[pslot][ticket_of(a, t, batches).nr] - e0;
+        const int32_t ne = s_ptr[pslot][ticket_of(a, t - a.t0, batches).nr] - e0;
         if (ne > kStage) return;  // read straight from global memory instead
         for (int i = threadIdx.x; i < ne; i += blockDim.x)
             cp_async4(&s_idx[islot][i], a.idx + e0 + i);
     };
 
-    // prologue: tickets 0..2 of this CTA, pointers of 0 and 1, list of 0
-    if (threadIdx.x < 3) s_tk[threadIdx.x] = atomicAdd(a.ticket_ctr, 1);
+    // prologue: three consecutive tickets, pointers of the first two, list of the first
+    if (threadIdx.x == 0) {
+        const int32_t t = atomicAdd(ticket_ctr, 3);
+        for (int k = 0; k < 3; ++k) take(k, t + k);
+    }
     __syncthreads();
-    stage_ptr(s_tk[0], 0);
+    stage_ptr(0, 0);
     cp_async_commit();
-    stage_ptr(s_tk[1], 1);
+    stage_ptr(1, 1);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    stage_idx(s_tk[0], 0, 0);
+    stage_idx(0, 0, 0);
     cp_async_commit();
     for (int it = 0;; ++it) {
         // ticket it's list and ticket it+1's pointers are in
         cp_async_wait<0>();
         __syncthreads();
         const int32_t t = s_tk[it & 3];
-        if (t >= n_tickets) break;  // tickets are taken in order: no later one is ours
+        if (t >= n_tickets) break;  // this CTA's tickets increase: no later one is below the end
+        const RowArgs &a = jobs[s_jb[it & 3]];
         const int ps = it % 3, is = it & 1;
-        if (threadIdx.x == 0) s_tk[(it + 3) & 3] = atomicAdd(a.ticket_ctr, 1);
-        stage_ptr(s_tk[(it + 2) & 3], (it + 2) % 3);
-        stage_idx(s_tk[(it + 1) & 3], (it + 1) % 3, (it + 1) & 1);
+        if (threadIdx.x == 0) take((it + 3) & 3, atomicAdd(ticket_ctr, 1));
+        stage_ptr((it + 2) & 3, (it + 2) % 3);
+        stage_idx((it + 1) & 3, (it + 1) % 3, (it + 1) & 1);
         cp_async_commit();
 
-        const Ticket k = ticket_of(a, t, batches);
+        const int32_t batches = (a.n_rows + a.rows - 1) / a.rows;
+        const Ticket k = ticket_of(a, t - a.t0, batches);
         const int32_t *rp = s_ptr[ps];
         const int32_t e_base = rp[0], e_end = rp[k.nr];
         const int32_t *idx = (e_end - e_base <= kStage) ? s_idx[is] : a.idx + e_base;
@@ -209,6 +242,18 @@ __global__ void __launch_bounds__(kEncThreads, kCtasPerSm) k_rows(RowArgs a) {
         }
     }
     cp_async_wait<0>();
+}
+
+// one job, passed by value
+__global__ void __launch_bounds__(kEncThreads, kCtasPerSm)
+    k_rows(const __grid_constant__ RowArgs a, int32_t n_tickets, int32_t *ticket_ctr) {
+    rows_body(&a, 1, n_tickets, ticket_ctr);
+}
+
+// a batch of jobs (stripes) in device memory
+__global__ void __launch_bounds__(kEncThreads, kCtasPerSm)
+    k_rows_batch(const RowArgs *jobs, int n_jobs, int32_t n_tickets, int32_t *ticket_ctr) {
+    rows_body(jobs, n_jobs, n_tickets, ticket_ctr);
 }
 
 // ---- shared-memory slice encode --------------------------------------------
@@ -818,9 +863,10 @@ cudaError_t launch_encode(const fs_code *c, const void *data, void *parity, void
         a.n_rows = c->m;
         a.stream_out = 0;
         a.rows = 1;  // check rows are long: one per ticket keeps every SM busy
-        a.ticket_ctr = hdr + WS_COUNT_A;
+        a.t0 = 0;
         const int64_t tickets = (int64_t)n_chunks * c->m;
-        k_rows<<<grid_for(tickets, c->num_sms, ctas), kEncThreads, 0, s>>>(a);
+        k_rows<<<grid_for(tickets, c->num_sms, ctas), kEncThreads, 0, s>>>(a, (int32_t)tickets,
+                                                                          hdr + WS_COUNT_A);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -834,10 +880,112 @@ cudaError_t launch_encode(const fs_code *c, const void *data, void *parity, void
         a.n_rows = c->n;
         a.stream_out = 1;
         a.rows = kRows;
-        a.ticket_ctr = hdr + WS_COUNT_B;
+        a.t0 = 0;
         const int64_t tickets = (int64_t)n_chunks * ((c->n + kRows - 1) / kRows);
-        k_rows<<<grid_for(tickets, c->num_sms, ctas), kEncThreads, 0, s>>>(a);
+        k_rows<<<grid_for(tickets, c->num_sms, ctas), kEncThreads, 0, s>>>(a, (int32_t)tickets,
+                                                                          hdr + WS_COUNT_B);
         e = cudaGetLastError();
     }
     return e;
+}
+
+// ---- batched encode ----------------------------------------------------------
+// Every stripe of a batch becomes two row jobs (its precode rows, its LT rows);
+// one launch runs all precode jobs, a second all LT jobs (stream order makes
+// every parity final before an LT row reads it). Tickets run stripe by stripe.
+
+struct EncodeBatch {
+    RowArgs *d_pre = nullptr, *d_lt = nullptr;  // device job arrays
+    int n_pre = 0, n_lt = 0;
+    int32_t t_pre = 0, t_lt = 0;  // tickets of each launch
+    int32_t *d_ctr = nullptr;     // two ticket counters
+    int num_sms = 1, ctas = 1;
+};
+
+cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *data,
+                              void *const *parity, void *const *coded, int32_t n,
+                              EncodeBatch **out) {
+    *out = nullptr;
+    std::vector<RowArgs> pre, lt;
+    int64_t tp = 0, tl = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const fs_code *c = codes[i];
+        const int32_t n_chunks = encode_chunks(c);
+        RowArgs a{};
+        a.tw = c->tw;
+        a.n_chunks = n_chunks;
+        a.hints = 0;
+        if (c->m > 0) {
+            a.ptr = c->pre_ptr;
+            a.idx = c->pre_idx;
+            a.inA = static_cast<const uint4 *>(data[i]);
+            a.inB = nullptr;
+            a.split = c->b;
+            a.out = static_cast<uint4 *>(parity[i]);
+            a.n_rows = c->m;
+            a.stream_out = 0;
+            a.rows = 1;
+            a.t0 = (int32_t)tp;
+            tp += (int64_t)n_chunks * c->m;
+            pre.push_back(a);
+        }
+        if (c->n > 0) {
+            a.ptr = c->con_ptr;
+            a.idx = c->con_idx;
+            a.inA = static_cast<const uint4 *>(data[i]);
+            a.inB = static_cast<const uint4 *>(parity[i]);
+            a.split = c->b;
+            a.out = static_cast<uint4 *>(coded[i]);
+            a.n_rows = c->n;
+            a.stream_out = 1;
+            a.rows = kRows;
+            a.t0 = (int32_t)tl;
+            tl += (int64_t)n_chunks * ((c->n + kRows - 1) / kRows);
+            lt.push_back(a);
+        }
+        if (tp >= INT32_MAX - 4096 || tl >= INT32_MAX - 4096) return cudaErrorInvalidValue;
+    }
+    EncodeBatch *b = new EncodeBatch();
+    b->n_pre = (int)pre.size();
+    b->n_lt = (int)lt.size();
+    b->t_pre = (int32_t)tp;
+    b->t_lt = (int32_t)tl;
+    b->num_sms = n > 0 ? codes[0]->num_sms : 1;
+    b->ctas = n > 0 ? std::min(codes[0]->gather_ctas, kCtasPerSm) : 1;
+    cudaError_t e = cudaMalloc(&b->d_ctr, 2 * sizeof(int32_t));
+    if (e == cudaSuccess && !pre.empty()) e = cudaMalloc(&b->d_pre, sizeof(RowArgs) * pre.size());
+    if (e == cudaSuccess && !lt.empty()) e = cudaMalloc(&b->d_lt, sizeof(RowArgs) * lt.size());
+    if (e == cudaSuccess && !pre.empty())
+        e = cudaMemcpy(b->d_pre, pre.data(), sizeof(RowArgs) * pre.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !lt.empty())
+        e = cudaMemcpy(b->d_lt, lt.data(), sizeof(RowArgs) * lt.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        encode_batch_free(b);
+        return e;
+    }
+    *out = b;
+    return cudaSuccess;
+}
+
+cudaError_t encode_batch_run(const EncodeBatch *b, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, 2 * sizeof(int32_t), s);
+    if (e == cudaSuccess && b->t_pre > 0) {
+        k_rows_batch<<<grid_for(b->t_pre, b->num_sms, b->ctas), kEncThreads, 0, s>>>(
+            b->d_pre, b->n_pre, b->t_pre, b->d_ctr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && b->t_lt > 0) {
+        k_rows_batch<<<grid_for(b->t_lt, b->num_sms, b->ctas), kEncThreads, 0, s>>>(
+            b->d_lt, b->n_lt, b->t_lt, b->d_ctr + 1);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+void encode_batch_free(EncodeBatch *b) {
+    if (!b) return;
+    cudaFree(b->d_pre);
+    cudaFree(b->d_lt);
+    cudaFree(b->d_ctr);
+    delete b;
 }

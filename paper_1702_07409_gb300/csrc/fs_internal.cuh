@@ -65,6 +65,21 @@ struct fs_code {
 // Builds the slice encode tables of c (host arrays of the joint graph);
 // leaves sl_slots = 0 when the code does not fit.
 cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t *con_idx);
+
+// ---- batches of stripes (device plans built once, run many times) ---------
+struct EncodeBatch;
+cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *data,
+                              void *const *parity, void *const *coded, int32_t n,
+                              EncodeBatch **out);
+cudaError_t encode_batch_run(const EncodeBatch *b, cudaStream_t s);
+void encode_batch_free(EncodeBatch *b);
+struct DecodeBatch;
+cudaError_t decode_batch_plan(const fs_code *const *codes, const void *const *coded,
+                              const uint8_t *const *erased, void *const *data_out,
+                              uint8_t *const *unrecovered, int32_t *const *n_unrecovered,
+                              void *const *ws, int32_t n, DecodeBatch **out);
+cudaError_t decode_batch_run(const DecodeBatch *b, cudaStream_t s);
+void decode_batch_free(DecodeBatch *b);
 void free_slice_tables(fs_code *c);
 
 constexpr int kRecipeSeg = 8;  // recipe entries one payload thread gathers at once

@@ -44,6 +44,9 @@
 //   shared-memory accumulators before the block is written.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "fs_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -284,7 +287,7 @@ struct DpgPlace {
     int32_t bytes;
 };
 
-__global__ void __launch_bounds__(kDpgThreads, 1) k_dpg(DpgArgs a, DpgPlace pl) {
+__device__ __forceinline__ void dpg_body(const DpgArgs &a, const DpgPlace &pl) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int4 s_warp4[2][32];
     __shared__ int4 s_len;
@@ -400,6 +403,15 @@ __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg(DpgArgs a, DpgPlace pl) 
     finish_dpg(a, cur, known, &s_cnt, &s_cnt_data);
 }
 
+__global__ void __launch_bounds__(kDpgThreads, 1) k_dpg(DpgArgs a, DpgPlace pl) { dpg_body(a, pl); }
+
+// one CTA per stripe of a batch
+__global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_batch(const DpgArgs *as, const DpgPlace *ps) {
+    const DpgArgs a = as[blockIdx.x];
+    const DpgPlace pl = ps[blockIdx.x];
+    dpg_body(a, pl);
+}
+
 DpgPlace plan_dpg(const fs_code *c) {
     DpgPlace p;
     const int64_t K = c->k_int + 1, G = c->n_con + 1;
@@ -448,7 +460,7 @@ __device__ __forceinline__ void red_add_shared(uint32_t *p, uint32_t v) {
     asm volatile("red.shared.add.u32 [%0], %1;\n" ::"r"(smem_addr_u(p)), "r"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCompactPlace pl) {
+__device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgCompactPlace &pl) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int4 s_warp4[2][32];
     __shared__ int4 s_len;
@@ -576,6 +588,18 @@ __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCo
         advance(cur, nt, len);
     }
     finish_dpg(a, cur, known, &s_cnt, &s_cnt_data);
+}
+
+__global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCompactPlace pl) {
+    dpg_compact_body(a, pl);
+}
+
+// one CTA per stripe of a batch
+__global__ void __launch_bounds__(kDpgThreads, 1)
+    k_dpg_compact_batch(const DpgArgs *as, const DpgCompactPlace *ps) {
+    const DpgArgs a = as[blockIdx.x];
+    const DpgCompactPlace pl = ps[blockIdx.x];
+    dpg_compact_body(a, pl);
 }
 
 // Shared-memory layout of k_dpg_compact, or bytes = -1 when the code does not
@@ -761,12 +785,12 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-__global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
+__device__ __forceinline__ void peel_body(const PeelArgs &a, int64_t slice) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) uint64_t mb_pairs[3];
     __shared__ int s_ok;
     const int L = a.L;
-    const int64_t w0 = (int64_t)blockIdx.x * L;
+    const int64_t w0 = slice * L;
     const int lanes = (int)min((int64_t)L, a.tw - w0);
     const int nv = (lanes + kPeelV - 1) / kPeelV;  // word pairs of this slice
     const int32_t nl = a.hdr[WS_N_LEVELS];
@@ -902,6 +926,15 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) { peel_body(a, blockIdx.x); }
+
+// one CTA per (stripe, slice) item of a batch
+__global__ void __launch_bounds__(kPeelThreads, 1) k_peel_batch(const PeelArgs *as, const int2 *items) {
+    const int2 it = items[blockIdx.x];
+    const PeelArgs a = as[it.x];
+    peel_body(a, it.y);
+}
+
 size_t peel_smem_bytes(int64_t L) {
     return (size_t)(kStageLevels + 1) * 32 + (size_t)3 * kStagePairs * kRec * 4 +
            (size_t)3 * kStageSegs * 4 + (size_t)3 * (kStageRecipe / 4) * 4 +
@@ -911,8 +944,10 @@ size_t peel_smem_bytes(int64_t L) {
 
 }  // namespace
 
-cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws, uint8_t *unrecovered,
-                       int32_t *n_unrecovered, cudaStream_t s) {
+namespace {
+
+DpgArgs dpg_args(const fs_code *c, const uint8_t *erased, uint8_t *ws, uint8_t *unrecovered,
+                 int32_t *n_unrecovered) {
     const DecodeLayout L = decode_layout(c);
     DpgArgs a;
     a.con_ptr = c->con_ptr;
@@ -944,6 +979,14 @@ cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws, uin
     a.hdr = reinterpret_cast<int32_t *>(ws);
     a.unrecovered = unrecovered;
     a.n_unrecovered = n_unrecovered;
+    return a;
+}
+
+}  // namespace
+
+cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws, uint8_t *unrecovered,
+                       int32_t *n_unrecovered, cudaStream_t s) {
+    const DpgArgs a = dpg_args(c, erased, ws, unrecovered, n_unrecovered);
     const DpgCompactPlace cp = plan_dpg_compact(c);
     if (c->dpg_compact && cp.bytes >= 0) {
         if (cp.bytes > 48 * 1024) {
@@ -964,8 +1007,20 @@ cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws, uin
     return cudaGetLastError();
 }
 
-cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_t *ws,
-                        cudaStream_t s) {
+namespace {
+
+// slice width: every slice in flight at once (peel_ctas CTAs per SM), a whole
+// number of word pairs, at most kPeelLmax words
+int64_t peel_slice_words(const fs_code *c) {
+    const int64_t ctas = (int64_t)c->num_sms * c->peel_ctas;
+    int64_t Lw = (c->tw + ctas - 1) / ctas;
+    Lw = (Lw + kPeelV - 1) / kPeelV * kPeelV;
+    if (Lw > kPeelLmax) Lw = kPeelLmax;
+    if (Lw < kPeelV) Lw = kPeelV;
+    return Lw;
+}
+
+PeelArgs peel_args(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_t *ws) {
     const DecodeLayout L = decode_layout(c);
     PeelArgs a;
     a.coded = coded;
@@ -983,14 +1038,16 @@ cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, u
     a.tw = c->tw;
     a.hints = c->l2_hints;
     a.status = reinterpret_cast<int32_t *>(ws) + WS_STATUS;
-    // slice width: every slice in flight at once (peel_ctas CTAs per SM),
-    // a whole number of word pairs, at most kPeelLmax words
-    const int64_t ctas = (int64_t)c->num_sms * c->peel_ctas;
-    int64_t Lw = (c->tw + ctas - 1) / ctas;
-    Lw = (Lw + kPeelV - 1) / kPeelV * kPeelV;
-    if (Lw > kPeelLmax) Lw = kPeelLmax;
-    if (Lw < kPeelV) Lw = kPeelV;
-    a.L = (int32_t)Lw;
+    a.L = (int32_t)peel_slice_words(c);
+    return a;
+}
+
+}  // namespace
+
+cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_t *ws,
+                        cudaStream_t s) {
+    const PeelArgs a = peel_args(c, coded, data_out, ws);
+    const int64_t Lw = a.L;
     const size_t smem = peel_smem_bytes(Lw);
     cudaError_t e =
         cudaFuncSetAttribute(k_peel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1000,4 +1057,114 @@ cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, u
     const int64_t n_slices = (c->tw + Lw - 1) / Lw;
     k_peel<<<(unsigned)n_slices, threads, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// ---- batched decode ----------------------------------------------------------
+// The symbolic pass of every stripe (one CTA each, compact form where it fits)
+// in one launch per form, then the payload of every (stripe, byte slice) item
+// in one launch; each item walks all levels of its stripe's path for its slice.
+
+struct DecodeBatch {
+    DpgArgs *d_dc = nullptr;
+    DpgCompactPlace *d_pc = nullptr;
+    int n_c = 0, smem_c = 0;
+    DpgArgs *d_dg = nullptr;
+    DpgPlace *d_pg = nullptr;
+    int n_g = 0, smem_g = 0;
+    PeelArgs *d_peel = nullptr;
+    int2 *d_items = nullptr;
+    int n_items = 0;
+    size_t smem_p = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t upload_vec(T **dst, const std::vector<T> &v) {
+    if (v.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc(dst, sizeof(T) * v.size());
+    if (e == cudaSuccess) e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
+}  // namespace
+
+cudaError_t decode_batch_plan(const fs_code *const *codes, const void *const *coded,
+                              const uint8_t *const *erased, void *const *data_out,
+                              uint8_t *const *unrecovered, int32_t *const *n_unrecovered,
+                              void *const *ws, int32_t n, DecodeBatch **out) {
+    *out = nullptr;
+    std::vector<DpgArgs> dc, dg;
+    std::vector<DpgCompactPlace> pc;
+    std::vector<DpgPlace> pg;
+    std::vector<PeelArgs> peel;
+    std::vector<int2> items;
+    DecodeBatch *b = new DecodeBatch();
+    for (int32_t i = 0; i < n; ++i) {
+        const fs_code *c = codes[i];
+        uint8_t *w = static_cast<uint8_t *>(ws[i]);
+        const DpgArgs a = dpg_args(c, erased[i], w, unrecovered[i], n_unrecovered[i]);
+        const DpgCompactPlace cp = plan_dpg_compact(c);
+        if (c->dpg_compact && cp.bytes >= 0) {
+            dc.push_back(a);
+            pc.push_back(cp);
+            b->smem_c = std::max(b->smem_c, (int)cp.bytes);
+        } else {
+            const DpgPlace pl = plan_dpg(c);
+            dg.push_back(a);
+            pg.push_back(pl);
+            b->smem_g = std::max(b->smem_g, (int)pl.bytes);
+        }
+        const PeelArgs pa = peel_args(c, static_cast<const uint4 *>(coded[i]),
+                                      static_cast<uint4 *>(data_out[i]), w);
+        peel.push_back(pa);
+        const int64_t slices = (c->tw + pa.L - 1) / pa.L;
+        if ((int64_t)items.size() + slices >= INT32_MAX) {
+            decode_batch_free(b);
+            return cudaErrorInvalidValue;
+        }
+        for (int64_t k = 0; k < slices; ++k) items.push_back(make_int2(i, (int)k));
+        b->smem_p = std::max(b->smem_p, peel_smem_bytes(pa.L));
+    }
+    b->n_c = (int)dc.size();
+    b->n_g = (int)dg.size();
+    b->n_items = (int)items.size();
+    cudaError_t e = upload_vec(&b->d_dc, dc);
+    if (e == cudaSuccess) e = upload_vec(&b->d_pc, pc);
+    if (e == cudaSuccess) e = upload_vec(&b->d_dg, dg);
+    if (e == cudaSuccess) e = upload_vec(&b->d_pg, pg);
+    if (e == cudaSuccess) e = upload_vec(&b->d_peel, peel);
+    if (e == cudaSuccess) e = upload_vec(&b->d_items, items);
+    if (e == cudaSuccess && b->smem_c > 48 * 1024)
+        e = cudaFuncSetAttribute(k_dpg_compact_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 b->smem_c);
+    if (e == cudaSuccess && b->smem_g > 48 * 1024)
+        e = cudaFuncSetAttribute(k_dpg_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, b->smem_g);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_peel_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)b->smem_p);
+    if (e != cudaSuccess) {
+        decode_batch_free(b);
+        return e;
+    }
+    *out = b;
+    return cudaSuccess;
+}
+
+cudaError_t decode_batch_run(const DecodeBatch *b, cudaStream_t s) {
+    if (b->n_c > 0) k_dpg_compact_batch<<<b->n_c, kDpgThreads, (size_t)b->smem_c, s>>>(b->d_dc, b->d_pc);
+    if (b->n_g > 0) k_dpg_batch<<<b->n_g, kDpgThreads, (size_t)b->smem_g, s>>>(b->d_dg, b->d_pg);
+    if (b->n_items > 0) k_peel_batch<<<b->n_items, kPeelThreads, b->smem_p, s>>>(b->d_peel, b->d_items);
+    return cudaGetLastError();
+}
+
+void decode_batch_free(DecodeBatch *b) {
+    if (!b) return;
+    cudaFree(b->d_dc);
+    cudaFree(b->d_pc);
+    cudaFree(b->d_dg);
+    cudaFree(b->d_pg);
+    cudaFree(b->d_peel);
+    cudaFree(b->d_items);
+    delete b;
 }

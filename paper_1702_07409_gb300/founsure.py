@@ -27,7 +27,16 @@ WS_STATUS_OFFSET = 0
 EXPORTS = ("fs_code_create", "fs_code_destroy", "fs_code_info", "fs_code_set_tuning",
            "fs_workspace_bytes",
            "fs_encode", "fs_encode_static", "fs_encode_rows", "fs_decode", "fs_decode_schedule",
-           "fs_decode_payload", "fs_decode_path", "fs_update", "fs_repair", "fs_status_string")
+           "fs_decode_payload", "fs_decode_path", "fs_update", "fs_repair",
+           "fs_batch_create", "fs_batch_run", "fs_batch_destroy", "fs_status_string")
+
+
+class _Stripe(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("d_data", ctypes.c_void_p),
+                ("d_parity", ctypes.c_void_p), ("d_coded", ctypes.c_void_p),
+                ("d_erased", ctypes.c_void_p), ("d_data_out", ctypes.c_void_p),
+                ("d_unrecovered", ctypes.c_void_p), ("d_n_unrecovered", ctypes.c_void_p),
+                ("d_ws", ctypes.c_void_p)]
 
 
 class FounsureError(RuntimeError):
@@ -84,6 +93,13 @@ def lib() -> ctypes.CDLL:
         L.fs_update.restype = ctypes.c_int
         L.fs_repair.argtypes = [vp, vp, i32, vp, vp, vp, vp, vp]
         L.fs_repair.restype = ctypes.c_int
+        L.fs_batch_create.argtypes = [ctypes.POINTER(_Stripe), i32, ctypes.c_int,
+                                      ctypes.POINTER(vp)]
+        L.fs_batch_create.restype = ctypes.c_int
+        L.fs_batch_run.argtypes = [vp, vp]
+        L.fs_batch_run.restype = ctypes.c_int
+        L.fs_batch_destroy.argtypes = [vp]
+        L.fs_batch_destroy.restype = None
         L.fs_status_string.argtypes = [ctypes.c_int]
         L.fs_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -265,3 +281,47 @@ class Code:
     def repair(self, lost, n_lost: int, data, parity, coded, ws, stream=None) -> None:
         _check(lib().fs_repair(self._h, _addr(lost), n_lost, _addr(data), _addr(parity),
                                _addr(coded), _addr(ws), _stream(stream)), "fs_repair")
+
+
+class Batch:
+    """fs_batch: many stripes (each with its own Code) encoded or decoded in a
+    fixed number of launches. `stripes` is a list of dicts with the fs_stripe
+    fields as tensors: encode {code, data, parity, coded}; decode {code,
+    coded, erased, data_out, unrecovered, n_unrecovered, ws}. The tensors are
+    kept alive by the batch; run() only enqueues (capturable in a CUDA
+    graph)."""
+
+    def __init__(self, stripes, op: int):
+        self._keep = stripes
+        arr = (_Stripe * max(len(stripes), 1))()
+        for i, s in enumerate(stripes):
+            code = s["code"]
+            if op == OP_ENCODE:
+                code._need(s["data"], code.b * code.t, "data")
+                code._need(s.get("parity"), code.m * code.t, "parity")
+                code._need(s["coded"], code.n * code.t, "coded")
+            elif op == OP_DECODE:  # other ops are left to the library to reject
+                code._need(s["coded"], code.n * code.t, "coded")
+                code._need(s["data_out"], code.b * code.t, "data_out")
+                code._need(s["ws"], code.workspace_bytes(OP_DECODE), "ws")
+            arr[i] = _Stripe(code._h, _addr(s.get("data")), _addr(s.get("parity")),
+                             _addr(s.get("coded")), _addr(s.get("erased")),
+                             _addr(s.get("data_out")), _addr(s.get("unrecovered")),
+                             _addr(s.get("n_unrecovered")), _addr(s.get("ws")))
+        h = ctypes.c_void_p()
+        _check(lib().fs_batch_create(arr, len(stripes), op, ctypes.byref(h)), "fs_batch_create")
+        self._h = h
+
+    def run(self, stream=None) -> None:
+        _check(lib().fs_batch_run(self._h, _stream(stream)), "fs_batch_run")
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().fs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
