@@ -632,6 +632,108 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+def run_serving(args):
+    """Requests served from device-resident stripes (paper_1702_07409_gb300.serve):
+    Poisson arrivals (mean 2000 requests/s, seeded exponential gaps) of encode
+    60% / decode 25% / update 10% / repair 5%; stripe sizes log-uniform in
+    [1, 256] MiB rounded to powers of two (so codes are reused), t = 16 or 64
+    KiB, n = 1.3 k, RSD(0.05, 0.01); decodes erase 10-25% of the target's coded
+    blocks, updates rewrite 1% of its data blocks, repairs recompute 5% of its
+    coded blocks; decode / update / repair pick a resident stripe at random
+    from a pre-populated pool; admission under a 120 GB budget. Continuous
+    batching is compared with one request per launch on the same stream of
+    requests."""
+    import torch
+    from paper_1702_07409_gb300.serve import Request, Server, latency_stats
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    budget = int(args.budget_gb * 1e9)
+    sizes = [1 << (20 + j) for j in range(9)]  # 1 MiB .. 256 MiB
+
+    def draw(n_req, meta):
+        """meta: stripe id -> (k, n) of the resident pool; grows with encodes.
+        The same seed every time: both serving modes see the same stream."""
+        rng = np.random.default_rng(gen.SEED_GRAPH + 5 + rank)
+        reqs, sid, t_now = [], 1 << 20, 0.0
+        live = list(meta)
+        for i in range(n_req):
+            t_now += float(rng.exponential(1.0 / args.rate))
+            u = rng.random()
+            if u < 0.60:
+                size = sizes[int(np.clip(np.round(rng.uniform(0, 8)), 0, 8))]
+                t = int(rng.choice([16384, 65536]))
+                reqs.append(Request(i, "encode", t_now, k=size // t, t=t, target=sid, seed=10**6 + i))
+                meta[sid] = (size // t, int(round(1.3 * (size // t))))
+                live.append(sid)
+                sid += 1
+            elif u < 0.85:
+                reqs.append(Request(i, "decode", t_now, target=int(rng.choice(live)), seed=2 * 10**6 + i,
+                                    erase_frac=float(rng.uniform(0.10, 0.25))))
+            elif u < 0.95:  # 1% of the target's data blocks rewritten
+                tg = int(rng.choice(live))
+                reqs.append(Request(i, "update", t_now, target=tg, seed=3 * 10**6 + i,
+                                    n_update=max(1, meta[tg][0] // 100)))
+            else:  # 5% of the target's coded blocks lost
+                tg = int(rng.choice(live))
+                reqs.append(Request(i, "repair", t_now, target=tg, seed=4 * 10**6 + i,
+                                    n_lost=max(1, meta[tg][1] // 20)))
+        return reqs
+
+    def serve(batching):
+        srv = Server(budget, device=device, streams=3 if batching else 1, batching=batching)
+        for size in sizes:  # every code the stream can ask for, built before the clock starts
+            for t in (16384, 65536):
+                srv.code_for(size // t, t)
+        meta = {}
+        prng = np.random.default_rng(77 + rank)
+        for p in range(args.pool):
+            size = sizes[int(prng.integers(0, 9))]
+            t = int(prng.choice([16384, 65536]))
+            srv.add_resident(p, size // t, t, seed=500 + p)
+            meta[p] = (size // t, srv.stripes[p].n)
+        reqs = draw(args.requests, meta)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reqs = srv.run(reqs, realtime=True)
+        wall = time.perf_counter() - t0
+        served = [r for r in reqs if r.done is not None and not r.out.get("dropped")
+                  and not r.out.get("rejected")]
+        bytes_ = 0
+        for r in served:
+            if r.kind == "encode":
+                bytes_ += r.k * r.t
+            elif r.kind == "decode":
+                bytes_ += int(r.out["data_out"].numel())
+        span = max(r.done for r in served) if served else wall
+        res = dict(latency_stats(reqs), gbs=round(bytes_ / span / 1e9, 2), span_s=round(span, 3),
+                   waves=srv.n_waves, peak_gb=round(srv.peak / 1e9, 2), evictions=srv.evictions,
+                   dropped=sum(1 for r in reqs if r.out.get("dropped")),
+                   rejected=sum(1 for r in reqs if r.out.get("rejected")))
+        srv.close()
+        return res
+
+    with ClockSampler(local) as clk:
+        batched = serve(True)
+    single = serve(False)
+    clocks = clk.summary()
+    line = {
+        "metric": "served source GB/s, p50/p99 latency", "value": batched["gbs"], "unit": "GB/s",
+        "n_gpus": world, "steps": args.requests, "warmup": 0, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded device random bytes, splitmix64 graphs, Poisson arrivals)",
+        "config": {"workload": "serving: Poisson %g requests/s, encode 60 / decode 25 / update 10 / "
+                               "repair 5 %%, stripes 1-256 MiB (powers of two), t 16 or 64 KiB, "
+                               "n = 1.3 k, budget %g GB, pool %d" % (args.rate, args.budget_gb, args.pool),
+                   "requests": args.requests},
+        "batched": batched, "one_request_per_launch": single,
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                   "reasons": clocks["reasons"]},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -648,9 +750,14 @@ def main():
     ap.add_argument("--peel-ctas", type=int, default=0, help="tuning knob (1..8)")
     ap.add_argument("--gather-ctas", type=int, default=0, help="tuning knob (1..16)")
 
-    ap.add_argument("--workload", default="stripe", choices=["stripe", "batched"],
+    ap.add_argument("--workload", default="stripe", choices=["stripe", "batched", "serving"],
                     help="stripe: the precoded stripe step (default); batched: many uneven "
-                         "stripes through fs_batch vs per-stripe calls")
+                         "stripes through fs_batch vs per-stripe calls; serving: a Poisson "
+                         "stream of requests on resident stripes")
+    ap.add_argument("--requests", type=int, default=2000, help="requests of --workload serving")
+    ap.add_argument("--rate", type=float, default=2000.0, help="mean arrivals per second (serving)")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="HBM budget (serving)")
+    ap.add_argument("--pool", type=int, default=64, help="pre-populated stripes (serving)")
     ap.add_argument("--stripes", type=int, default=512, help="stripes of --workload batched")
     ap.add_argument("--block-bytes", type=int, default=65536,
                     help="block size t (default 65536; smaller only for profiling captures)")
@@ -661,6 +768,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_gpu(args)
 

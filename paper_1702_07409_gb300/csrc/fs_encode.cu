@@ -952,13 +952,10 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
     b->t_lt = (int32_t)tl;
     b->num_sms = n > 0 ? codes[0]->num_sms : 1;
     b->ctas = n > 0 ? std::min(codes[0]->gather_ctas, kCtasPerSm) : 1;
-    cudaError_t e = cudaMalloc(&b->d_ctr, 2 * sizeof(int32_t));
-    if (e == cudaSuccess && !pre.empty()) e = cudaMalloc(&b->d_pre, sizeof(RowArgs) * pre.size());
-    if (e == cudaSuccess && !lt.empty()) e = cudaMalloc(&b->d_lt, sizeof(RowArgs) * lt.size());
-    if (e == cudaSuccess && !pre.empty())
-        e = cudaMemcpy(b->d_pre, pre.data(), sizeof(RowArgs) * pre.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !lt.empty())
-        e = cudaMemcpy(b->d_lt, lt.data(), sizeof(RowArgs) * lt.size(), cudaMemcpyHostToDevice);
+    const int32_t zero[2] = {0, 0};
+    cudaError_t e = plan_upload(&b->d_ctr, zero, 2);
+    if (e == cudaSuccess) e = plan_upload(&b->d_pre, pre.data(), pre.size());
+    if (e == cudaSuccess) e = plan_upload(&b->d_lt, lt.data(), lt.size());
     if (e != cudaSuccess) {
         encode_batch_free(b);
         return e;
@@ -984,8 +981,8 @@ cudaError_t encode_batch_run(const EncodeBatch *b, cudaStream_t s) {
 
 void encode_batch_free(EncodeBatch *b) {
     if (!b) return;
-    cudaFree(b->d_pre);
-    cudaFree(b->d_lt);
-    cudaFree(b->d_ctr);
+    plan_free(b->d_pre);
+    plan_free(b->d_lt);
+    plan_free(b->d_ctr);
     delete b;
 }

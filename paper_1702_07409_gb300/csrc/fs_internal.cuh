@@ -67,6 +67,26 @@ struct fs_code {
 cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t *con_idx);
 
 // ---- batches of stripes (device plans built once, run many times) ---------
+// Device copy of a host array for a batch plan: stream-ordered allocation and
+// copy on a private non-blocking stream, so planning does not wait for work
+// other streams have in flight. Free with plan_free.
+template <typename T>
+cudaError_t plan_upload(T **dst, const T *src, size_t count) {
+    *dst = nullptr;
+    if (count == 0) return cudaSuccess;
+    cudaStream_t s;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaMallocAsync(reinterpret_cast<void **>(dst), sizeof(T) * count, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(*dst, src, sizeof(T) * count, cudaMemcpyHostToDevice, s);
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    return e != cudaSuccess ? e : e2;
+}
+template <typename T>
+void plan_free(T *p) {
+    if (p) cudaFree(p);
+}
 struct EncodeBatch;
 cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *data,
                               void *const *parity, void *const *coded, int32_t n,

@@ -1081,10 +1081,7 @@ namespace {
 
 template <typename T>
 cudaError_t upload_vec(T **dst, const std::vector<T> &v) {
-    if (v.empty()) return cudaSuccess;
-    cudaError_t e = cudaMalloc(dst, sizeof(T) * v.size());
-    if (e == cudaSuccess) e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
-    return e;
+    return plan_upload(dst, v.data(), v.size());
 }
 
 }  // namespace
@@ -1160,11 +1157,11 @@ cudaError_t decode_batch_run(const DecodeBatch *b, cudaStream_t s) {
 
 void decode_batch_free(DecodeBatch *b) {
     if (!b) return;
-    cudaFree(b->d_dc);
-    cudaFree(b->d_pc);
-    cudaFree(b->d_dg);
-    cudaFree(b->d_pg);
-    cudaFree(b->d_peel);
-    cudaFree(b->d_items);
+    plan_free(b->d_dc);
+    plan_free(b->d_pc);
+    plan_free(b->d_dg);
+    plan_free(b->d_pg);
+    plan_free(b->d_peel);
+    plan_free(b->d_items);
     delete b;
 }

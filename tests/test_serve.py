@@ -1,0 +1,84 @@
+"""Serving loop: each request's result is the same whether it runs alone
+(one request per launch, in arrival order) or mixed into continuously formed
+batches with other requests; admission never exceeds the memory budget."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(seed=7, n_req=48):
+    from paper_1702_07409_gb300.serve import Request
+    rng = np.random.default_rng(seed)
+    reqs, sid = [], 100
+    t_now = 0.0
+    live = list(range(6))  # the pre-populated stripes 0..5
+    for i in range(n_req):
+        t_now += float(rng.exponential(1e-4))
+        u = rng.random()
+        if u < 0.4:
+            k = int(rng.choice([32, 64, 128, 300]))
+            t = int(rng.choice([64, 1024, 4096]))
+            reqs.append(Request(i, "encode", t_now, k=k, t=t, target=sid, seed=1000 + i))
+            live.append(sid)
+            sid += 1
+        elif u < 0.75:
+            reqs.append(Request(i, "decode", t_now, target=int(rng.choice(live)), seed=2000 + i,
+                                erase_frac=float(rng.uniform(0.05, 0.25))))
+        elif u < 0.9:
+            reqs.append(Request(i, "update", t_now, target=int(rng.choice(live)), seed=3000 + i,
+                                n_update=2))
+        else:
+            reqs.append(Request(i, "repair", t_now, target=int(rng.choice(live)), seed=4000 + i,
+                                n_lost=3))
+    return reqs
+
+
+def _serve(batching, budget=1 << 30):
+    import torch
+    from paper_1702_07409_gb300.serve import Server
+    srv = Server(budget, streams=3 if batching else 1, batching=batching)
+    for i in range(6):
+        srv.add_resident(i, k=int([32, 64, 128, 300, 64, 32][i]), t=int([64, 1024, 4096, 64, 4096, 1024][i]),
+                         seed=10 + i)
+    reqs = srv.run(_requests(), realtime=False)
+    torch.cuda.synchronize()
+    dec = {r.rid: (r.out["data_out"].cpu().numpy(), int(r.out["n_unrecovered"].item()))
+           for r in reqs if r.kind == "decode" and not r.out.get("dropped")}
+    state = {sid: (st.data.cpu().numpy(), st.coded.cpu().numpy()) for sid, st in srv.stripes.items()}
+    peak, budget_ = srv.peak, srv.budget
+    waves = srv.n_waves
+    srv.close()
+    return dec, state, peak, budget_, reqs, waves
+
+
+def test_mixed_equals_alone_and_budget_holds():
+    dec_m, st_m, peak_m, budget, reqs_m, waves_m = _serve(True)
+    dec_a, st_a, peak_a, _, reqs_a, waves_a = _serve(False)
+    assert waves_m < waves_a  # requests were grouped
+    assert peak_m <= budget and peak_a <= budget
+    assert dec_m.keys() == dec_a.keys() and len(dec_m) > 5
+    for rid in dec_m:
+        assert np.array_equal(dec_m[rid][0], dec_a[rid][0])
+        assert dec_m[rid][1] == dec_a[rid][1]
+    assert st_m.keys() == st_a.keys()
+    for sid in st_m:
+        assert np.array_equal(st_m[sid][0], st_a[sid][0])
+        assert np.array_equal(st_m[sid][1], st_a[sid][1])
+    assert all(r.done is not None for r in reqs_m)
+
+
+def test_decode_recovers_the_stripe_data():
+    """A decode of a stripe with 10% erased returns its data (recovered
+    blocks) and zeros (unrecovered ones)."""
+    import torch
+    from paper_1702_07409_gb300.serve import Request, Server
+    srv = Server(1 << 30, streams=2)
+    srv.add_resident(0, k=128, t=4096, seed=5)
+    data = srv.stripes[0].data.clone()
+    reqs = srv.run([Request(0, "decode", 0.0, target=0, seed=9, erase_frac=0.1)], realtime=False)
+    torch.cuda.synchronize()
+    out = reqs[0].out["data_out"]
+    un = reqs[0].out["unrecovered"].bool()
+    assert torch.equal(out[~un], data[~un]) and bool((out[un] == 0).all())
+    srv.close()
