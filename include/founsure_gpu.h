@@ -122,6 +122,11 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
  *                        memory, else 16-byte slices; 2: always 16-byte
  *                        slices; 3: always 32-byte slices (when they fit);
  *                        0: row-gather encode through L2
+ *   FS_TUNE_ROWS_PER_TICKET 1..16 (default 16): coded rows per work ticket of
+ *                        the row-gather encode (single calls and batches);
+ *                        fewer rows per ticket keep the tickets in flight on a
+ *                        narrower byte range of every block (better L2 reuse
+ *                        of the gathered inputs) at more scheduling cost
  * Returns FS_ERR_INVALID for an unknown knob or an out-of-range value. Not
  * thread-safe against concurrent hot calls on the same code. */
 #define FS_TUNE_PEEL_CTAS   1
@@ -129,6 +134,7 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
 #define FS_TUNE_DPG_COMPACT 3
 #define FS_TUNE_L2_HINTS    4
 #define FS_TUNE_ENCODE_SLICES 5
+#define FS_TUNE_ROWS_PER_TICKET 6
 fs_status fs_code_set_tuning(fs_code *code, int knob, int value);
 
 /* Bytes of caller-provided device workspace that op needs. n_items is the
@@ -296,6 +302,12 @@ fs_status fs_batch_create(const fs_stripe *stripes, int32_t n, int op, fs_batch 
  * synchronisation: a run can be captured in a CUDA graph and the graph
  * replayed). FS_ERR_INVALID when the current device is not the batch's. */
 fs_status fs_batch_run(const fs_batch *batch, void *stream);
+
+/* The device status of the batch's last run (blocking: waits for the
+ * copy): FS_OK, or FS_ERR_TIMEOUT when a bounded wait of the encode gave up.
+ * A decode batch reports its stripes' statuses in their workspaces (as
+ * fs_decode does) and always gives FS_OK here. */
+fs_status fs_batch_status(const fs_batch *batch, int32_t *status);
 
 /* Waits for the device, then frees the batch's device arrays. */
 void fs_batch_destroy(fs_batch *batch);

@@ -1,11 +1,12 @@
 """Autotuner for batches of stripes.
 
 The batched encode runs a persistent row-gather kernel whose resident CTAs
-per SM (FS_TUNE_GATHER_CTAS, 1..5 for that kernel) trade latency hiding
-against L2 working set; which is best depends on the stripes' block sizes and
-degrees. tune_batch_encode times a batch once per candidate on the GPU it
-will run on and keeps the fastest (it sets that knob on every code, so
-batches created afterwards use it).
+per SM (FS_TUNE_GATHER_CTAS, 1..4 for that kernel) and rows per work ticket
+(FS_TUNE_ROWS_PER_TICKET) trade latency hiding against the L2 working set;
+which is best depends on the stripes' block sizes and degrees.
+tune_batch_encode times a batch once per candidate on the GPU it will run on
+and keeps the fastest (it sets the knobs on every code, so batches created
+afterwards use them).
 """
 from __future__ import annotations
 
@@ -24,26 +25,32 @@ def _cuda_timer(fn, runs: int) -> float:
     return e0.elapsed_time(e1) / runs
 
 
-def tune_batch_encode(codes, make_batch, candidates=(2, 3, 4, 5), runs: int = 3,
-                      timer=_cuda_timer) -> dict:
+def tune_batch_encode(codes, make_batch, candidates=((2, 16), (3, 16), (4, 16), (3, 8), (4, 8),
+                                                     (4, 4), (4, 2)),
+                      runs: int = 3, timer=_cuda_timer) -> dict:
     """Times make_batch() (an encode Batch over `codes`) for each candidate
-    value of the CTAs-per-SM knob and keeps the fastest.
+    (CTAs per SM, rows per ticket) of the row-gather kernel and keeps the
+    fastest (fewer rows per ticket narrow the byte range the tickets in
+    flight cover, which decides how much of the gathered inputs L2 keeps).
 
     codes       the stripes' Code objects
-    make_batch  builds the batch (after the knob is set on every code)
-    Returns {"knob", "best", "ms": {candidate: ms per run}}."""
+    make_batch  builds the batch (after the knobs are set on every code)
+    Returns {"knobs", "best", "ms": {"ctas x rows": ms per run}}."""
     from . import founsure as fs
     times = {}
-    for c in candidates:
+    for cand in candidates:
+        ctas, rows = cand
         for code in codes:
-            code.set_tuning(fs.TUNE_GATHER_CTAS, c)
+            code.set_tuning(fs.TUNE_GATHER_CTAS, ctas)
+            code.set_tuning(fs.TUNE_ROWS_PER_TICKET, rows)
         batch = make_batch()
         try:
-            times[c] = float(timer(batch.run, runs))
+            times[cand] = float(timer(batch.run, runs))
         finally:
             batch.close()
     best = min(times, key=times.get)
     for code in codes:
-        code.set_tuning(fs.TUNE_GATHER_CTAS, best)
-    return {"knob": "gather_ctas", "best": best,
-            "ms": {str(k): round(v, 4) for k, v in times.items()}}
+        code.set_tuning(fs.TUNE_GATHER_CTAS, best[0])
+        code.set_tuning(fs.TUNE_ROWS_PER_TICKET, best[1])
+    return {"knobs": ["gather_ctas", "rows_per_ticket"], "best": list(best),
+            "ms": {"%dx%d" % k: round(v, 4) for k, v in times.items()}}

@@ -164,6 +164,7 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     c->dpg_compact = 1;
     c->l2_hints = 0;
     c->encode_slices = 1;
+    c->rows_per_ticket = 16;
     cudaError_t e = cudaGetDevice(&c->device);
     int v = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c->device);
@@ -215,6 +216,10 @@ FS_API fs_status fs_code_set_tuning(fs_code *c, int knob, int value) {
         case FS_TUNE_DPG_COMPACT:
             if (value != 0 && value != 1) return FS_ERR_INVALID;
             c->dpg_compact = value;
+            return FS_OK;
+        case FS_TUNE_ROWS_PER_TICKET:
+            if (value < 1 || value > 16) return FS_ERR_INVALID;
+            c->rows_per_ticket = value;
             return FS_OK;
         case FS_TUNE_ENCODE_SLICES:
             if (value < 0 || value > 3) return FS_ERR_INVALID;

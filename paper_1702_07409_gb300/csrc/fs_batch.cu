@@ -91,6 +91,14 @@ FS_API fs_status fs_batch_run(const fs_batch *bt, void *stream) {
     return e == cudaSuccess ? FS_OK : FS_ERR_CUDA;
 }
 
+FS_API fs_status fs_batch_status(const fs_batch *bt, int32_t *status) {
+    if (!bt || !status) return FS_ERR_INVALID;
+    *status = FS_OK;
+    if (bt->op == FS_OP_ENCODE && bt->enc && encode_batch_status_word(bt->enc, status) != 0)
+        return FS_ERR_CUDA;
+    return FS_OK;
+}
+
 FS_API void fs_batch_destroy(fs_batch *bt) {
     if (!bt) return;
     cudaDeviceSynchronize();

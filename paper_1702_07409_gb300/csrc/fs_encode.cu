@@ -49,7 +49,7 @@ constexpr int kEncV = 1;                      // words per thread per chunk
 constexpr int kChunkW = kEncV * kEncThreads;  // 16-byte words per chunk (4 KiB)
 constexpr int kRows = 16;                     // rows per ticket
 constexpr int kStage = 2048;                  // neighbour entries of one ticket staged
-constexpr int kCtasPerSm = 5;
+constexpr int kCtasPerSm = 4;
 
 }  // namespace
 
@@ -506,6 +506,90 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
     }
 }
 
+// Batch form: persistent CTAs take items (stripe, slices [s0, s1)) from a
+// counter. A CTA reloads the stripe's tables and zero slots only when its
+// item's stripe differs from the previous one; within an item the copies of
+// the next slice land under the arithmetic of the current one. 16-byte slots,
+// two buffers; buffers start at the same place for every stripe (the largest
+// stripe's buffer size apart), the tables after them.
+__global__ void __launch_bounds__(kSliceThreads, 1)
+    k_slices_batch(const SliceArgs *as, const CUtensorMap *maps, const int4 *items, int n_items,
+                   int32_t max_slots, int32_t *item_ctr, int32_t *status) {
+    constexpr int V = 1;
+    extern __shared__ __align__(256) unsigned char s_raw[];
+    uint4 *slot0 = reinterpret_cast<uint4 *>(s_raw + ((kSlotAlign - (saddr(s_raw) & (kSlotAlign - 1))) & (kSlotAlign - 1)));
+    const size_t buf_words = (size_t)max_slots * V;
+    uint4 *s_tab = slot0 + 2 * buf_words;
+    __shared__ uint64_t s_bar[2];
+    __shared__ int32_t s_item, s_ok;
+    __shared__ int s_ctr[2];
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&s_bar[i])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        s_ctr[0] = 0;
+        s_ctr[1] = 0;
+    }
+    uint32_t uses0 = 0, uses1 = 0;  // completed phases of each buffer's barrier (thread 0)
+    int cur = -1;                   // stripe whose tables are loaded
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(item_ctr, 1);
+        __syncthreads();  // also: every warp is done with the previous item
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int4 item = items[it];
+        const SliceArgs a = as[item.x];
+        const CUtensorMap *map = maps + item.x;
+        const unsigned char *tp = reinterpret_cast<const unsigned char *>(s_tab);
+        SliceTables tb;
+        tb.grp = reinterpret_cast<const int2 *>(tp);
+        tb.grow = reinterpret_cast<const uint16_t *>(tp + a.off_row);
+        tb.gidx = reinterpret_cast<const uint16_t *>(tp + a.off_idx);
+        if (item.x != cur) {  // this stripe's tables, zero slots and zeroed parity slots
+            for (int32_t i = threadIdx.x; i < a.tab_words; i += blockDim.x) s_tab[i] = __ldg(a.tab + i);
+            for (int i = threadIdx.x; i < 2 * 8 * V; i += blockDim.x)
+                slot0[(size_t)(i / (8 * V)) * buf_words + (size_t)a.zbase * V + i % (8 * V)] =
+                    make_uint4(0, 0, 0, 0);
+            for (int bb = 0; bb < 2; ++bb) zero_parities<V>(a, slot0 + (size_t)bb * buf_words);
+            cur = item.x;
+        }
+        const int n_one = a.n_grp_a, n_two = a.n_grp - a.n_grp_a;
+        if (threadIdx.x == 0) issue_slice<V>(map, a, item.y, slot0, &s_bar[0]);
+        __syncthreads();  // tables and zero slots in place
+        for (int32_t t = item.y, j = 0; t < item.z; ++t, ++j) {
+            const int b = j & 1;
+            uint4 *slot = slot0 + (size_t)b * buf_words;
+            if (threadIdx.x == 0) {
+                int ok = wait_phase(&s_bar[b], (b ? uses1 : uses0) & 1) ? 1 : 0;
+                if (!ok) {  // a second bounded wait for the copies in flight, then give up
+                    atomicExch(status, (int32_t)FS_ERR_TIMEOUT);
+                    wait_phase(&s_bar[b], (b ? uses1 : uses0) & 1);
+                }
+                s_ok = ok;
+            }
+            __syncthreads();  // slice t is in; every warp has left slice t - 1
+            if (!s_ok) return;
+            if (b) ++uses1;
+            else ++uses0;
+            if (threadIdx.x == 0) {
+                s_ctr[1] = 0;
+                if (t + 1 < item.z) issue_slice<V>(map, a, t + 1, slot0 + (size_t)(b ^ 1) * buf_words, &s_bar[b ^ 1]);
+            }
+            zero_parities<V>(a, slot0 + (size_t)(b ^ 1) * buf_words);
+            const int64_t w0 = (int64_t)t * V;
+            drain(&s_ctr[0], n_one, [&](int i) { row_group<V>(a, tb, slot, i, w0); });
+            __syncthreads();  // the parity slots are complete
+            if (threadIdx.x == 0) s_ctr[0] = 0;
+            for (int i = threadIdx.x; i < a.m * V; i += blockDim.x) {
+                const int jj = i / V, h = i - jj * V;
+                if (w0 + h < a.tw) a.parity[(int64_t)jj * a.tw + w0 + h] = slot[unit_of<V>(a.bpad + jj, h)];
+            }
+            drain(&s_ctr[1], n_two, [&](int i) { row_group<V>(a, tb, slot, a.n_grp_a + i, w0); });
+        }
+    }
+}
+
 using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
 
 EncodeTiledFn tensor_map_encoder() {
@@ -780,12 +864,53 @@ namespace {
 // arithmetic) matter more than the slot width, so: 32-byte slots (full-sector
 // copies and stores) when two buffers of them fit, else 16-byte slots, with
 // two buffers when they fit.
+// The launch arguments of a code's slice encode with v words per slot and
+// nbuf buffers; false when no tensor map can be made.
+bool slice_setup(const fs_code *c, const void *data, void *parity, void *coded, int v, int nbuf,
+                 SliceArgs *a, CUtensorMap *map) {
+    EncodeTiledFn encode = tensor_map_encoder();
+    if (!encode) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)c->t, (cuuint64_t)c->b};
+    const cuuint64_t strides[1] = {(cuuint64_t)c->t};
+    const cuuint32_t box[2] = {(cuuint32_t)(16 * v), (cuuint32_t)c->sl_box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(data), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               v == 2 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    a->tab = reinterpret_cast<const uint4 *>(c->sl_tab);
+    a->tab_words = c->sl_tab_bytes / 16;
+    a->off_row = c->sl_off_row;
+    a->off_idx = c->sl_off_idx;
+    a->parity = static_cast<uint4 *>(parity);
+    a->coded = static_cast<uint4 *>(coded);
+    a->m = c->m;
+    a->n_grp = c->sl_n_grp;
+    a->n_grp_p = c->sl_n_grp_p;
+    a->n_grp_a = c->sl_n_grp_a;
+    a->bpad = c->sl_bpad;
+    a->zbase = c->sl_zbase;
+    a->slots = c->sl_slots;
+    a->box_rows = c->sl_box_rows;
+    a->n_boxes = c->sl_bpad / c->sl_box_rows;
+    a->nbuf = nbuf;
+    a->tw = c->tw;
+    a->n_slices = (int32_t)((c->tw + v - 1) / v);
+    a->ticket = nullptr;
+    a->status = nullptr;
+    return true;
+}
+
+// Slice encode of the whole code; false (nothing launched) when it does not apply.
+// Two slot buffers (the next slice's copies land under the current slice's
+// arithmetic) matter more than the slot width, so: 32-byte slots (full-sector
+// copies and stores) when two buffers of them fit, else 16-byte slots, with
+// two buffers when they fit.
 bool launch_slices(const fs_code *c, const void *data, void *parity, void *coded, int32_t *hdr,
                    cudaStream_t s, cudaError_t *err) {
     *err = cudaSuccess;
     if (!c->encode_slices || c->sl_slots == 0 || c->t >= ((int64_t)1 << 31)) return false;
-    EncodeTiledFn encode = tensor_map_encoder();
-    if (!encode) return false;
     int v = c->encode_slices == 2   ? 1
             : c->encode_slices == 3 ? 2
             : (slice_smem_bytes(c, 2, 2) <= c->smem_optin && c->tw >= 2 ? 2 : 1);
@@ -793,34 +918,8 @@ bool launch_slices(const fs_code *c, const void *data, void *parity, void *coded
     const int nbuf = slice_smem_bytes(c, v, 2) <= c->smem_optin ? 2 : 1;
     const size_t smem = slice_smem_bytes(c, v, nbuf);
     CUtensorMap map;
-    const cuuint64_t dims[2] = {(cuuint64_t)c->t, (cuuint64_t)c->b};
-    const cuuint64_t strides[1] = {(cuuint64_t)c->t};
-    const cuuint32_t box[2] = {(cuuint32_t)(16 * v), (cuuint32_t)c->sl_box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(data), dims, strides, box,
-               estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               v == 2 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return false;
     SliceArgs a;
-    a.tab = reinterpret_cast<const uint4 *>(c->sl_tab);
-    a.tab_words = c->sl_tab_bytes / 16;
-    a.off_row = c->sl_off_row;
-    a.off_idx = c->sl_off_idx;
-    a.parity = static_cast<uint4 *>(parity);
-    a.coded = static_cast<uint4 *>(coded);
-    a.m = c->m;
-    a.n_grp = c->sl_n_grp;
-    a.n_grp_p = c->sl_n_grp_p;
-    a.n_grp_a = c->sl_n_grp_a;
-    a.bpad = c->sl_bpad;
-    a.zbase = c->sl_zbase;
-    a.slots = c->sl_slots;
-    a.box_rows = c->sl_box_rows;
-    a.n_boxes = c->sl_bpad / c->sl_box_rows;
-    a.nbuf = nbuf;
-    a.tw = c->tw;
-    a.n_slices = (int32_t)((c->tw + v - 1) / v);
+    if (!slice_setup(c, data, parity, coded, v, nbuf, &a, &map)) return false;
     a.ticket = hdr + WS_COUNT_A;
     a.status = hdr + WS_STATUS;
     auto kern = v == 2 ? k_slices<2> : k_slices<1>;
@@ -879,9 +978,9 @@ cudaError_t launch_encode(const fs_code *c, const void *data, void *parity, void
         a.out = static_cast<uint4 *>(coded);
         a.n_rows = c->n;
         a.stream_out = 1;
-        a.rows = kRows;
+        a.rows = c->rows_per_ticket;
         a.t0 = 0;
-        const int64_t tickets = (int64_t)n_chunks * ((c->n + kRows - 1) / kRows);
+        const int64_t tickets = (int64_t)n_chunks * ((c->n + a.rows - 1) / a.rows);
         k_rows<<<grid_for(tickets, c->num_sms, ctas), kEncThreads, 0, s>>>(a, (int32_t)tickets,
                                                                           hdr + WS_COUNT_B);
         e = cudaGetLastError();
@@ -895,12 +994,22 @@ cudaError_t launch_encode(const fs_code *c, const void *data, void *parity, void
 // every parity final before an LT row reads it). Tickets run stripe by stripe.
 
 struct EncodeBatch {
-    RowArgs *d_pre = nullptr, *d_lt = nullptr;  // device job arrays
+    RowArgs *d_pre = nullptr, *d_lt = nullptr;  // device job arrays (row-gather stripes)
     int n_pre = 0, n_lt = 0;
     int32_t t_pre = 0, t_lt = 0;  // tickets of each launch
-    int32_t *d_ctr = nullptr;     // two ticket counters
+    SliceArgs *d_sl = nullptr;    // slice stripes: arguments, tensor maps, items
+    CUtensorMap *d_maps = nullptr;
+    int4 *d_items = nullptr;
+    int n_items = 0;
+    int32_t max_slots = 0;
+    size_t smem_sl = 0;
+    int32_t *d_ctr = nullptr;     // ticket counters (precode, LT), item counter, status
     int num_sms = 1, ctas = 1;
 };
+
+int32_t encode_batch_status_word(const EncodeBatch *b, int32_t *out) {
+    return cudaMemcpy(out, b->d_ctr + 3, sizeof(int32_t), cudaMemcpyDeviceToHost) == cudaSuccess ? 0 : -1;
+}
 
 cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *data,
                               void *const *parity, void *const *coded, int32_t n,
@@ -908,7 +1017,45 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
     *out = nullptr;
     std::vector<RowArgs> pre, lt;
     int64_t tp = 0, tl = 0;
+    // stripes whose slice layout fits (16-byte slots, two buffers) go to the
+    // batch slice kernel; the layout of a launch is the largest buffers and
+    // the largest tables of its stripes, so stripes are added while that fits
+    const size_t budget = n > 0 ? codes[0]->smem_optin : 0;
+    std::vector<int32_t> order;
+    for (int32_t i = 0; i < n; ++i)
+        if (codes[i]->encode_slices && codes[i]->sl_slots > 0 && codes[i]->t < ((int64_t)1 << 31))
+            order.push_back(i);
+    std::sort(order.begin(), order.end(),
+              [&](int32_t x, int32_t y) { return codes[x]->sl_tab_bytes < codes[y]->sl_tab_bytes; });
+    std::vector<char> sliced(n, 0);
+    int32_t max_slots = 0, max_tab = 0;
+    for (int32_t i : order) {
+        const int32_t ms = std::max(max_slots, codes[i]->sl_slots);
+        const int32_t mt = std::max(max_tab, codes[i]->sl_tab_bytes);
+        if ((size_t)2 * ms * 16 + (size_t)mt + kSlotAlign > budget) continue;
+        max_slots = ms;
+        max_tab = mt;
+        sliced[i] = 1;
+    }
+    std::vector<SliceArgs> sl;
+    std::vector<CUtensorMap> maps;
+    std::vector<int4> items;
+    constexpr int32_t kItemSlices = 32;
     for (int32_t i = 0; i < n; ++i) {
+        if (!sliced[i]) continue;
+        SliceArgs a;
+        CUtensorMap map;
+        if (!slice_setup(codes[i], data[i], parity[i], coded[i], 1, 2, &a, &map)) {
+            sliced[i] = 0;
+            continue;
+        }
+        for (int32_t s0 = 0; s0 < a.n_slices; s0 += kItemSlices)
+            items.push_back(make_int4((int)sl.size(), s0, std::min(a.n_slices, s0 + kItemSlices), 0));
+        sl.push_back(a);
+        maps.push_back(map);
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        if (sliced[i]) continue;
         const fs_code *c = codes[i];
         const int32_t n_chunks = encode_chunks(c);
         RowArgs a{};
@@ -938,9 +1085,9 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
             a.out = static_cast<uint4 *>(coded[i]);
             a.n_rows = c->n;
             a.stream_out = 1;
-            a.rows = kRows;
+            a.rows = c->rows_per_ticket;
             a.t0 = (int32_t)tl;
-            tl += (int64_t)n_chunks * ((c->n + kRows - 1) / kRows);
+            tl += (int64_t)n_chunks * ((c->n + a.rows - 1) / a.rows);
             lt.push_back(a);
         }
         if (tp >= INT32_MAX - 4096 || tl >= INT32_MAX - 4096) return cudaErrorInvalidValue;
@@ -952,10 +1099,19 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
     b->t_lt = (int32_t)tl;
     b->num_sms = n > 0 ? codes[0]->num_sms : 1;
     b->ctas = n > 0 ? std::min(codes[0]->gather_ctas, kCtasPerSm) : 1;
-    const int32_t zero[2] = {0, 0};
-    cudaError_t e = plan_upload(&b->d_ctr, zero, 2);
+    const int32_t zero[4] = {0, 0, 0, 0};
+    b->n_items = (int)items.size();
+    b->max_slots = max_slots;
+    b->smem_sl = (size_t)2 * max_slots * 16 + (size_t)max_tab + kSlotAlign;
+    cudaError_t e = plan_upload(&b->d_ctr, zero, 4);
     if (e == cudaSuccess) e = plan_upload(&b->d_pre, pre.data(), pre.size());
     if (e == cudaSuccess) e = plan_upload(&b->d_lt, lt.data(), lt.size());
+    if (e == cudaSuccess) e = plan_upload(&b->d_sl, sl.data(), sl.size());
+    if (e == cudaSuccess) e = plan_upload(&b->d_maps, maps.data(), maps.size());
+    if (e == cudaSuccess) e = plan_upload(&b->d_items, items.data(), items.size());
+    if (e == cudaSuccess && b->n_items > 0)
+        e = cudaFuncSetAttribute(k_slices_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)b->smem_sl);
     if (e != cudaSuccess) {
         encode_batch_free(b);
         return e;
@@ -965,7 +1121,13 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
 }
 
 cudaError_t encode_batch_run(const EncodeBatch *b, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, 2 * sizeof(int32_t), s);
+    cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, 4 * sizeof(int32_t), s);
+    if (e == cudaSuccess && b->n_items > 0) {
+        const int g = b->n_items < b->num_sms ? b->n_items : b->num_sms;
+        k_slices_batch<<<g, kSliceThreads, b->smem_sl, s>>>(b->d_sl, b->d_maps, b->d_items, b->n_items,
+                                                           b->max_slots, b->d_ctr + 2, b->d_ctr + 3);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess && b->t_pre > 0) {
         k_rows_batch<<<grid_for(b->t_pre, b->num_sms, b->ctas), kEncThreads, 0, s>>>(
             b->d_pre, b->n_pre, b->t_pre, b->d_ctr);
@@ -983,6 +1145,9 @@ void encode_batch_free(EncodeBatch *b) {
     if (!b) return;
     plan_free(b->d_pre);
     plan_free(b->d_lt);
+    plan_free(b->d_sl);
+    plan_free(b->d_maps);
+    plan_free(b->d_items);
     plan_free(b->d_ctr);
     delete b;
 }

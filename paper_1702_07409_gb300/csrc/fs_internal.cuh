@@ -41,6 +41,7 @@ struct fs_code {
     int dpg_compact;      // 1: symbolic peel in the compact shared-memory form when it fits
     int l2_hints;         // 1: L2 evict-last / evict-first hints on the gathers
     int encode_slices;    // 1: shared-memory slice encode when the code fits
+    int rows_per_ticket;  // coded rows per work ticket of the row-gather encode (1..16)
     // slice encode tables (present when sl_slots > 0): every input block has
     // a 16-byte shared-memory slot per byte slice; data block v is slot v,
     // parity j is slot sl_bpad + j
@@ -92,6 +93,7 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
                               void *const *parity, void *const *coded, int32_t n,
                               EncodeBatch **out);
 cudaError_t encode_batch_run(const EncodeBatch *b, cudaStream_t s);
+int32_t encode_batch_status_word(const EncodeBatch *b, int32_t *out);  // 0, or -1 on a CUDA error
 void encode_batch_free(EncodeBatch *b);
 struct DecodeBatch;
 cudaError_t decode_batch_plan(const fs_code *const *codes, const void *const *coded,

@@ -21,6 +21,7 @@ DECODE_JOINT, DECODE_TWO_PASS = 0, 1
 OP_ENCODE, OP_DECODE, OP_UPDATE, OP_REPAIR = 0, 1, 2, 3
 TUNE_PEEL_CTAS, TUNE_GATHER_CTAS, TUNE_DPG_COMPACT, TUNE_L2_HINTS = 1, 2, 3, 4
 TUNE_ENCODE_SLICES = 5
+TUNE_ROWS_PER_TICKET = 6
 WS_STATUS_OFFSET = 0
 
 #: every symbol declared in include/founsure_gpu.h
@@ -28,7 +29,8 @@ EXPORTS = ("fs_code_create", "fs_code_destroy", "fs_code_info", "fs_code_set_tun
            "fs_workspace_bytes",
            "fs_encode", "fs_encode_static", "fs_encode_rows", "fs_decode", "fs_decode_schedule",
            "fs_decode_payload", "fs_decode_path", "fs_update", "fs_repair",
-           "fs_batch_create", "fs_batch_run", "fs_batch_destroy", "fs_status_string")
+           "fs_batch_create", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
+           "fs_status_string")
 
 
 class _Stripe(ctypes.Structure):
@@ -98,6 +100,8 @@ def lib() -> ctypes.CDLL:
         L.fs_batch_create.restype = ctypes.c_int
         L.fs_batch_run.argtypes = [vp, vp]
         L.fs_batch_run.restype = ctypes.c_int
+        L.fs_batch_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+        L.fs_batch_status.restype = ctypes.c_int
         L.fs_batch_destroy.argtypes = [vp]
         L.fs_batch_destroy.restype = None
         L.fs_status_string.argtypes = [ctypes.c_int]
@@ -172,6 +176,12 @@ class Code:
         _check(rc, "fs_code_create")
         self._h = h
         self._lib = lib()
+
+    def status(self) -> int:
+        """Device status of the last run (blocking)."""
+        st = ctypes.c_int32(0)
+        _check(lib().fs_batch_status(self._h, ctypes.byref(st)), "fs_batch_status")
+        return int(st.value)
 
     def close(self) -> None:
         if getattr(self, "_h", None):
@@ -314,6 +324,12 @@ class Batch:
 
     def run(self, stream=None) -> None:
         _check(lib().fs_batch_run(self._h, _stream(stream)), "fs_batch_run")
+
+    def status(self) -> int:
+        """Device status of the last run (blocking)."""
+        st = ctypes.c_int32(0)
+        _check(lib().fs_batch_status(self._h, ctypes.byref(st)), "fs_batch_status")
+        return int(st.value)
 
     def close(self) -> None:
         if getattr(self, "_h", None):

@@ -94,6 +94,7 @@ def test_batch_encode_decode_match_the_oracle():
     enc.run()
     dec.run()
     torch.cuda.synchronize()
+    assert enc.status() == fs.FS_OK and dec.status() == fs.FS_OK
     stalls = 0
     for s in st:
         path = s.check_decode(s.check_encode())

@@ -300,3 +300,21 @@ def test_tuning_knobs_leave_results_unchanged(knob, value):
         _check_decode(case, cod, cd, _erased(case.n, 0.15, gen.SEED_ERASE + (s << 20)))
     with pytest.raises(fs.FounsureError):
         case.code.set_tuning(knob, 99)
+
+
+@pytest.mark.parametrize("rows", [1, 3, 16])
+def test_row_gather_encode_rows_per_ticket(rows):
+    """The row-gather encode (slices off) with 1, 3 or 16 coded rows per work
+    ticket, precoded and plain codes, ragged block size."""
+    fs = _fs()
+    for b, m, n, t in ((1500, 60, 2000, 4096 + 32), (300, 0, 400, 48)):
+        case = Case(b, m, n, t, gen.DIST_FINITE40)
+        case.code.set_tuning(fs.TUNE_ENCODE_SLICES, 0)
+        case.code.set_tuning(fs.TUNE_ROWS_PER_TICKET, rows)
+        _, p, cd = case.encode_gpu()
+        par, cod = oracle.encode(case.g, case.data, case.t)
+        assert np.array_equal(_host(cd), cod)
+        if m:
+            assert np.array_equal(_host(p), par)
+    with pytest.raises(fs.FounsureError):
+        case.code.set_tuning(fs.TUNE_ROWS_PER_TICKET, 17)
