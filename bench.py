@@ -197,8 +197,8 @@ class Stripe:
         self.nun_reads = []
 
     # launches of this library's kernels per step (encode 1: the slice
-    # kernel; decode 2: schedule + payload; update 6; repair 1)
-    LAUNCHES_PER_STEP = 10
+    # kernel; decode 2: schedule + payload; update 4; repair 1)
+    LAUNCHES_PER_STEP = 8
 
     @property
     def nun(self):

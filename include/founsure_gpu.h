@@ -312,6 +312,15 @@ fs_status fs_batch_status(const fs_batch *batch, int32_t *status);
 /* Waits for the device, then frees the batch's device arrays. */
 void fs_batch_destroy(fs_batch *batch);
 
+/* Shows the library's wait-timeout path (no paper counterpart; for
+ * failure-detection tests): enqueues one kernel whose bounded wait on an
+ * mbarrier can never be satisfied (it expects bytes no copy delivers); when
+ * the wait's iteration limit runs out the kernel writes FS_ERR_TIMEOUT to
+ * *d_status (device int32, 4-byte aligned) and returns, leaving the context
+ * usable. The payload and encode kernels bound their waits the same way and
+ * report FS_ERR_TIMEOUT in their status words. */
+fs_status fs_selftest_timeout(int32_t *d_status, void *stream);
+
 /* Static string naming a status. */
 const char *fs_status_string(fs_status s);
 

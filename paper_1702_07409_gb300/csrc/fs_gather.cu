@@ -118,30 +118,26 @@ __device__ __forceinline__ bool upd_ok(const UpdArgs &a) {
     return *(volatile int32_t *)a.status == FS_OK;
 }
 
-// mark[i] = -1, pmark[j] = cmark[g] = 0, list counts 0, status FS_OK
-__global__ void k_update_init(UpdArgs a) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i0 == 0) {
+// One CTA: mark[i] = -1, pmark[j] = cmark[g] = 0, list counts 0, status
+// FS_OK; then mark[idx[q]] = q (a repeated or out-of-range index flags the
+// call invalid).
+__global__ void __launch_bounds__(1024) k_update_init(UpdArgs a) {
+    if (threadIdx.x == 0) {
         *a.status = FS_OK;
         *a.n_plist = 0;
         *a.n_clist = 0;
     }
-    for (int64_t i = i0; i < a.b; i += stride) a.mark[i] = -1;
-    for (int64_t j = i0; j < a.m; j += stride) a.pmark[j] = 0;
-    for (int64_t g = i0; g < a.n; g += stride) a.cmark[g] = 0;
-}
-
-// mark[idx[q]] = q; a repeated or out-of-range index flags the call invalid
-__global__ void k_update_mark(UpdArgs a) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n_idx; q += stride) {
+    for (int64_t i = threadIdx.x; i < a.b; i += blockDim.x) a.mark[i] = -1;
+    for (int64_t j = threadIdx.x; j < a.m; j += blockDim.x) a.pmark[j] = 0;
+    for (int64_t g = threadIdx.x; g < a.n; g += blockDim.x) a.cmark[g] = 0;
+    __syncthreads();
+    for (int32_t q = threadIdx.x; q < a.n_idx; q += blockDim.x) {
         const int32_t i = a.idx[q];
         if (i < 0 || i >= a.b) {
             atomicExch(a.status, FS_ERR_INVALID);
             continue;
         }
-        if (atomicCAS(a.mark + i, -1, (int32_t)q) != -1) atomicExch(a.status, FS_ERR_INVALID);
+        if (atomicCAS(a.mark + i, -1, q) != -1) atomicExch(a.status, FS_ERR_INVALID);
     }
 }
 
@@ -191,17 +187,6 @@ k_update_delta(UpdArgs a, int32_t n_chunks) {
     }
 }
 
-// CTA per changed check j: the coded rows containing parity b + j are listed.
-__global__ void k_update_plist(UpdArgs a) {
-    if (!upd_ok(a)) return;
-    const int32_t np = *(volatile int32_t *)a.n_plist;
-    for (int32_t k = blockIdx.x; k < np; k += gridDim.x) {
-        const int32_t v = a.b + a.plist[k];
-        for (int32_t e = a.var_ptr[v] + threadIdx.x; e < a.var_ptr[v + 1]; e += blockDim.x)
-            touch(a, a.var_idx[e], true);
-    }
-}
-
 // Lists, in s_src, the deltas of the changed members among con_idx-style
 // entries [base, base + nb) (data block v: its delta if it was rewritten;
 // v >= b: parity v - b's delta if that check changed). Returns the count.
@@ -226,7 +211,8 @@ __device__ __forceinline__ int list_changed(const UpdArgs &a, const int32_t *mem
 }
 
 // changed parity j ^= XOR of the deltas of its changed members; pdelta_j
-// keeps that XOR. Tiles (listed check, chunk), chunk-major.
+// keeps that XOR; the chunk-0 tile of check j also lists the coded rows that
+// contain parity b + j. Tiles (listed check, chunk), chunk-major.
 __global__ void __launch_bounds__(kGatherThreads, 3)
 k_update_parity(UpdArgs a, int32_t n_chunks) {
     __shared__ const uint4 *s_src[kSrcBatch];
@@ -241,6 +227,11 @@ k_update_parity(UpdArgs a, int32_t n_chunks) {
         const int32_t j = a.plist[tile - (int64_t)chunk * np];
         const int32_t e0 = a.pre_ptr[j], e1 = a.pre_ptr[j + 1];
         const int64_t w0 = (int64_t)chunk * kChunkW, w1 = min(w0 + kChunkW, a.tw);
+        if (chunk == 0) {
+            const int32_t v = a.b + j;
+            for (int32_t e = a.var_ptr[v] + threadIdx.x; e < a.var_ptr[v + 1]; e += blockDim.x)
+                touch(a, a.var_idx[e], true);
+        }
         uint4 acc[kWpt];
 #pragma unroll
         for (int i = 0; i < kWpt; ++i) acc[i] = make_uint4(0, 0, 0, 0);
@@ -343,16 +334,12 @@ cudaError_t launch_update(const fs_code *c, const int32_t *idx, int32_t n_idx, c
     a.tw = c->tw;
     a.status = reinterpret_cast<int32_t *>(ws) + WS_STATUS;
 
-    int64_t nb = c->b > c->m ? c->b : c->m;
-    nb = nb > c->n ? nb : c->n;
-    k_update_init<<<grid_for((nb + 255) / 256, c->num_sms), 256, 0, s>>>(a);
+    k_update_init<<<1, 1024, 0, s>>>(a);
     if (n_idx > 0) {
-        k_update_mark<<<grid_for((n_idx + 255) / 256, c->num_sms), 256, 0, s>>>(a);
         const int32_t n_chunks = chunks_of(c->tw);
         k_update_delta<<<grid_for((int64_t)n_idx * n_chunks, c->num_sms), kGatherThreads, 0, s>>>(
             a, n_chunks);
         if (c->m > 0) {
-            k_update_plist<<<grid_for(c->m, c->num_sms), 128, 0, s>>>(a);
             k_update_parity<<<grid_for((int64_t)n_chunks * c->m, c->num_sms), kGatherThreads, 0, s>>>(
                 a, n_chunks);
         }

@@ -71,3 +71,33 @@ FS_API fs_status fs_encode_static(const fs_code *c, const void *d_data, void *d_
                             sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
     return e == cudaSuccess ? FS_OK : FS_ERR_CUDA;
 }
+
+namespace {
+
+// Waits on an mbarrier that expects bytes no copy will deliver, with the same
+// kind of bounded wait the payload and encode kernels use; when the bound
+// runs out it records FS_ERR_TIMEOUT and returns (nothing is in flight).
+__global__ void k_selftest_timeout(int32_t *status, long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(a) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], 16;\n" ::"r"(a) : "memory");
+    uint32_t done = 0;
+    for (long long i = 0; i < limit && !done; ++i)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a)
+            : "memory");
+    *status = done ? (int32_t)FS_OK : (int32_t)FS_ERR_TIMEOUT;
+}
+
+}  // namespace
+
+FS_API fs_status fs_selftest_timeout(int32_t *d_status, void *stream) {
+    if (!d_status || ((uintptr_t)d_status & 3u) != 0) return FS_ERR_INVALID;
+    k_selftest_timeout<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(d_status, 1ll << 16);
+    return cudaGetLastError() == cudaSuccess ? FS_OK : FS_ERR_CUDA;
+}

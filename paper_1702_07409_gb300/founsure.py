@@ -30,7 +30,7 @@ EXPORTS = ("fs_code_create", "fs_code_destroy", "fs_code_info", "fs_code_set_tun
            "fs_encode", "fs_encode_static", "fs_encode_rows", "fs_decode", "fs_decode_schedule",
            "fs_decode_payload", "fs_decode_path", "fs_update", "fs_repair",
            "fs_batch_create", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
-           "fs_status_string")
+           "fs_selftest_timeout", "fs_status_string")
 
 
 class _Stripe(ctypes.Structure):
@@ -104,6 +104,8 @@ def lib() -> ctypes.CDLL:
         L.fs_batch_status.restype = ctypes.c_int
         L.fs_batch_destroy.argtypes = [vp]
         L.fs_batch_destroy.restype = None
+        L.fs_selftest_timeout.argtypes = [vp, vp]
+        L.fs_selftest_timeout.restype = ctypes.c_int
         L.fs_status_string.argtypes = [ctypes.c_int]
         L.fs_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -341,3 +343,12 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def selftest_timeout(stream=None) -> int:
+    """fs_selftest_timeout: runs a kernel whose bounded wait always runs out
+    and returns the status it wrote (FS_ERR_TIMEOUT)."""
+    import torch
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    _check(lib().fs_selftest_timeout(_addr(st), _stream(stream)), "fs_selftest_timeout")
+    return int(st.item())

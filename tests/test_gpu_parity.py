@@ -318,3 +318,14 @@ def test_row_gather_encode_rows_per_ticket(rows):
             assert np.array_equal(_host(p), par)
     with pytest.raises(fs.FounsureError):
         case.code.set_tuning(fs.TUNE_ROWS_PER_TICKET, 17)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A wait that nothing will satisfy gives up after its limit, reports
+    FS_ERR_TIMEOUT, and the context still runs kernels afterwards."""
+    fs = _fs()
+    assert fs.selftest_timeout() == fs.FS_ERR_TIMEOUT
+    case = Case(100, 0, 150, 1024, gen.DIST_RSD, 0.1, 0.05)
+    _, _, cd = case.encode_gpu()
+    _, want = oracle.encode(case.g, case.data, case.t)
+    assert np.array_equal(_host(cd), want)
