@@ -270,6 +270,7 @@ struct SliceArgs {
     int32_t off_row, off_idx; // byte offsets inside tab
     uint4 *parity, *coded;
     int32_t m, n_grp, n_grp_p, n_grp_a, bpad, zbase, slots, box_rows, n_boxes, nbuf;
+    int32_t write_parity;     // 1: this part writes the parities out (the first part)
     int64_t tw;               // 16-byte words per block
     int32_t n_slices;         // byte slices of the stripe
     int32_t *ticket;          // workspace counter, zero at launch
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
         drain(&s_ctr[0], n_one, [&](int i) { row_group<V>(a, tb, slot, i, w0); });
         __syncthreads();  // the parity slots are complete
         if (threadIdx.x == 0) s_ctr[0] = 0;
-        for (int i = threadIdx.x; i < a.m * V; i += blockDim.x) {
+        for (int i = threadIdx.x; a.write_parity && i < a.m * V; i += blockDim.x) {
             const int j = i / V, h = i - j * V;
             if (w0 + h < a.tw) a.parity[(int64_t)j * a.tw + w0 + h] = slot[unit_of<V>(a.bpad + j, h)];
         }
@@ -514,12 +515,11 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
 // stripe's buffer size apart), the tables after them.
 __global__ void __launch_bounds__(kSliceThreads, 1)
     k_slices_batch(const SliceArgs *as, const CUtensorMap *maps, const int4 *items, int n_items,
-                   int32_t max_slots, int32_t *item_ctr, int32_t *status) {
+                   int32_t *item_ctr, int32_t *status) {
     constexpr int V = 1;
     extern __shared__ __align__(256) unsigned char s_raw[];
-    uint4 *slot0 = reinterpret_cast<uint4 *>(s_raw + ((kSlotAlign - (saddr(s_raw) & (kSlotAlign - 1))) & (kSlotAlign - 1)));
-    const size_t buf_words = (size_t)max_slots * V;
-    uint4 *s_tab = slot0 + 2 * buf_words;
+    // per stripe: its tables first, then its two slot buffers (256-byte aligned)
+    uint4 *s_tab = reinterpret_cast<uint4 *>(s_raw + ((kSlotAlign - (saddr(s_raw) & (kSlotAlign - 1))) & (kSlotAlign - 1)));
     __shared__ uint64_t s_bar[2];
     __shared__ int32_t s_item, s_ok;
     __shared__ int s_ctr[2];
@@ -541,6 +541,8 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
         const int4 item = items[it];
         const SliceArgs a = as[item.x];
         const CUtensorMap *map = maps + item.x;
+        uint4 *slot0 = s_tab + (((size_t)a.tab_words + 15) & ~(size_t)15);
+        const size_t buf_words = (size_t)a.slots * V;
         const unsigned char *tp = reinterpret_cast<const unsigned char *>(s_tab);
         SliceTables tb;
         tb.grp = reinterpret_cast<const int2 *>(tp);
@@ -581,7 +583,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
             drain(&s_ctr[0], n_one, [&](int i) { row_group<V>(a, tb, slot, i, w0); });
             __syncthreads();  // the parity slots are complete
             if (threadIdx.x == 0) s_ctr[0] = 0;
-            for (int i = threadIdx.x; i < a.m * V; i += blockDim.x) {
+            for (int i = threadIdx.x; a.write_parity && i < a.m * V; i += blockDim.x) {
                 const int jj = i / V, h = i - jj * V;
                 if (w0 + h < a.tw) a.parity[(int64_t)jj * a.tw + w0 + h] = slot[unit_of<V>(a.bpad + jj, h)];
             }
@@ -607,8 +609,10 @@ EncodeTiledFn tensor_map_encoder() {
 }
 
 size_t slice_smem_bytes(const fs_code *c, int v, int nbuf) {
-    // slot buffers, tables, alignment slack
-    return (size_t)nbuf * (size_t)c->sl_slots * 16 * v + (size_t)c->sl_tab_bytes + kSlotAlign;
+    // slot buffers, the largest part's tables, alignment slack
+    int32_t tab = 0;
+    for (int q = 0; q < c->sl_parts; ++q) tab = std::max(tab, c->sl_part[q].tab_bytes);
+    return (size_t)nbuf * (size_t)c->sl_slots * 16 * v + (size_t)tab + kSlotAlign;
 }
 
 int grid_for(int64_t n_tiles, int num_sms, int ctas_per_sm) {
@@ -681,6 +685,7 @@ std::vector<int> colour_edges(const std::vector<std::pair<int, int>> &edges, int
 
 cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t *con_idx) {
     c->sl_slots = 0;
+    c->sl_parts = 0;
     if (c->b < 1 || c->n < 1 || c->n >= kNoSlot || c->m >= kNoSlot) return cudaSuccess;
     const int32_t box_rows = c->b < 256 ? c->b : 256;
     const int64_t bpad = ((int64_t)c->b + box_rows - 1) / box_rows * box_rows;
@@ -713,149 +718,197 @@ cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t
         for (int32_t e = con_ptr[r]; e < con_ptr[r + 1]; ++e) in[(size_t)mp + r].push_back(slot_of(con_idx[e]));
     auto deg = [&](int32_t id) { return (int)in[id].size(); };
 
-    // rows into quarters of 8 (rows of about the same length, largest first,
-    // whose inputs spread evenly over the bank groups), quarters sorted by
-    // width and padded to whole warp groups
+    // Builds the tables of one part: the parity pieces (every part computes
+    // the parities its coded rows read) and coded rows [r_lo, r_hi): rows
+    // into quarters of 8 (rows of about the same length, largest first, whose
+    // inputs spread evenly over the bank groups), quarters sorted by width
+    // and padded to whole warp groups, then each quarter's inputs placed by
+    // an edge colouring. Returns false when the tables grow too large.
     struct Quarter {
         int32_t row[8];
         int delta;
     };
-    std::vector<Quarter> quarters;
-    std::vector<char> used((size_t)mp + n, 0);
-    auto build_quarters = [&](std::vector<int32_t> order) {
-        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return deg(x) > deg(y); });
-        std::vector<Quarter> qs;
-        constexpr int kWindow = 64;  // candidates looked at for each place
-        size_t pos = 0;
-        for (;;) {
-            while (pos < order.size() && used[order[pos]]) ++pos;
-            if (pos >= order.size()) break;
-            Quarter q;
-            std::fill(q.row, q.row + 8, -1);
-            int cnt[8] = {0};
-            const int dmax = deg(order[pos]);
-            for (int k = 0; k < 8; ++k) {
-                int32_t best = -1;
-                int best_key = 0, best_deg = 0;
-                int seen = 0;
-                for (size_t i = pos; i < order.size() && seen < (k == 0 ? 1 : kWindow); ++i) {
-                    const int32_t r = order[i];
-                    if (used[r]) continue;
-                    ++seen;
-                    int c2[8];
-                    std::copy(cnt, cnt + 8, c2);
-                    for (uint16_t sl : in[r]) ++c2[bank_group(sl)];
-                    const int key = std::max(*std::max_element(c2, c2 + 8), dmax);
-                    if (best < 0 || key < best_key || (key == best_key && deg(r) > best_deg)) {
-                        best = r;
-                        best_key = key;
-                        best_deg = deg(r);
-                    }
-                }
-                if (best < 0) break;
-                used[best] = 1;
-                q.row[k] = best;
-                for (uint16_t sl : in[best]) ++cnt[bank_group(sl)];
-            }
-            q.delta = std::max(*std::max_element(cnt, cnt + 8), dmax);
-            qs.push_back(q);
-        }
-        std::stable_sort(qs.begin(), qs.end(), [](const Quarter &x, const Quarter &y) { return x.delta > y.delta; });
-        while (qs.size() % 4) {  // empty quarters complete the last warp group
-            Quarter e;
-            std::fill(e.row, e.row + 8, -1);
-            e.delta = 0;
-            qs.push_back(e);
-        }
-        quarters.insert(quarters.end(), qs.begin(), qs.end());
+    struct HostPart {
+        std::vector<unsigned char> tab;
+        int32_t n_grp = 0, n_grp_p = 0, n_grp_a = 0, off_row = 0, off_idx = 0;
     };
-    // parity rows; coded rows that read no parity (computed beside the
-    // parities); coded rows that read one (after them)
-    std::vector<int32_t> set_p, set_a, set_b;
-    for (int32_t p = 0; p < mp; ++p) set_p.push_back(p);
-    for (int32_t r = 0; r < n; ++r) {
-        bool par = false;
-        for (int32_t e = con_ptr[r]; e < con_ptr[r + 1]; ++e) par |= con_idx[e] >= c->b;
-        (par ? set_b : set_a).push_back(mp + r);
-    }
-    build_quarters(set_p);
-    const int32_t n_grp_p = (int32_t)(quarters.size() / 4);
-    build_quarters(set_a);
-    const int32_t n_grp_a = (int32_t)(quarters.size() / 4);
-    build_quarters(set_b);
-    const int32_t n_grp = (int32_t)(quarters.size() / 4);
-    std::vector<int2> grp(n_grp);
-    int64_t total = 0;
-    for (int32_t gq = 0; gq < n_grp; ++gq) {
-        const int cols = quarters[(size_t)gq * 4].delta;  // sorted: the first is the widest
-        grp[gq] = make_int2((int32_t)total, cols);
-        total += 32 * (int64_t)cols;
-        if (total > (int64_t)1 << 24) return cudaSuccess;
-    }
-
-    auto al16 = [](int64_t x) { return (x + 15) & ~(int64_t)15; };
-    const int64_t off_row = al16((int64_t)sizeof(int2) * n_grp);
-    const int64_t off_idx = al16(off_row + 2 * 32 * (int64_t)n_grp);
-    const int64_t bytes = al16(off_idx + 2 * total);
-    if ((size_t)slots * 16 + (size_t)bytes + kSlotAlign > c->smem_optin) return cudaSuccess;
-
-    std::vector<unsigned char> tab((size_t)bytes, 0);
-    memcpy(tab.data(), grp.data(), sizeof(int2) * n_grp);
-    uint16_t *row = reinterpret_cast<uint16_t *>(tab.data() + off_row);
-    uint16_t *idx = reinterpret_cast<uint16_t *>(tab.data() + off_idx);
-    std::fill(row, row + 32 * (size_t)n_grp, kNoSlot);
-    std::fill(idx, idx + total, kNoSlot);
-    std::vector<std::pair<int, int>> edges;
-    std::vector<uint16_t> eslot;
-    for (size_t qi = 0; qi < quarters.size(); ++qi) {
-        const Quarter &q = quarters[qi];
-        const int32_t gq = (int32_t)(qi / 4), lane0 = 8 * (int32_t)(qi % 4);
-        edges.clear();
-        eslot.clear();
-        for (int p = 0; p < 8; ++p) {
-            if (q.row[p] < 0) continue;
-            // output id: the parity index, or the coded row
-            row[(size_t)gq * 32 + lane0 + p] = (uint16_t)(q.row[p] < mp ? q.row[p] / ks : q.row[p] - mp);
-            for (uint16_t sl : in[q.row[p]]) {
-                edges.emplace_back(p, bank_group(sl));
-                eslot.push_back(sl);
+    std::vector<char> used((size_t)mp + n, 0);
+    auto make_part = [&](int32_t r_lo, int32_t r_hi, HostPart &hp) -> bool {
+        std::vector<Quarter> quarters;
+        for (int32_t p = 0; p < mp; ++p) used[p] = 0;
+        for (int32_t r = r_lo; r < r_hi; ++r) used[(size_t)mp + r] = 0;
+        auto build_quarters = [&](std::vector<int32_t> order) {
+            std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return deg(x) > deg(y); });
+            std::vector<Quarter> qs;
+            constexpr int kWindow = 64;  // candidates looked at for each place
+            size_t pos = 0;
+            for (;;) {
+                while (pos < order.size() && used[order[pos]]) ++pos;
+                if (pos >= order.size()) break;
+                Quarter q;
+                std::fill(q.row, q.row + 8, -1);
+                int cnt[8] = {0};
+                const int dmax = deg(order[pos]);
+                for (int k = 0; k < 8; ++k) {
+                    int32_t best = -1;
+                    int best_key = 0, best_deg = 0;
+                    int seen = 0;
+                    for (size_t i = pos; i < order.size() && seen < (k == 0 ? 1 : kWindow); ++i) {
+                        const int32_t r = order[i];
+                        if (used[r]) continue;
+                        ++seen;
+                        int c2[8];
+                        std::copy(cnt, cnt + 8, c2);
+                        for (uint16_t sl : in[r]) ++c2[bank_group(sl)];
+                        const int key = std::max(*std::max_element(c2, c2 + 8), dmax);
+                        if (best < 0 || key < best_key || (key == best_key && deg(r) > best_deg)) {
+                            best = r;
+                            best_key = key;
+                            best_deg = deg(r);
+                        }
+                    }
+                    if (best < 0) break;
+                    used[best] = 1;
+                    q.row[k] = best;
+                    for (uint16_t sl : in[best]) ++cnt[bank_group(sl)];
+                }
+                q.delta = std::max(*std::max_element(cnt, cnt + 8), dmax);
+                qs.push_back(q);
             }
+            std::stable_sort(qs.begin(), qs.end(), [](const Quarter &x, const Quarter &y) { return x.delta > y.delta; });
+            while (qs.size() % 4) {  // empty quarters complete the last warp group
+                Quarter e;
+                std::fill(e.row, e.row + 8, -1);
+                e.delta = 0;
+                qs.push_back(e);
+            }
+            quarters.insert(quarters.end(), qs.begin(), qs.end());
+        };
+        // parity rows; coded rows that read no parity (computed beside the
+        // parities); coded rows that read one (after them)
+        std::vector<int32_t> set_p, set_a, set_b;
+        for (int32_t p = 0; p < mp; ++p) set_p.push_back(p);
+        for (int32_t r = r_lo; r < r_hi; ++r) {
+            bool par = false;
+            for (int32_t e = con_ptr[r]; e < con_ptr[r + 1]; ++e) par |= con_idx[e] >= c->b;
+            (par ? set_b : set_a).push_back(mp + r);
         }
-        const std::vector<int> col = colour_edges(edges, std::max(q.delta, 1));
-        for (size_t e = 0; e < edges.size(); ++e)
-            idx[(size_t)grp[gq].x + (size_t)col[e] * 32 + lane0 + edges[e].first] = eslot[e];
-        // empty cells of each column: the zero slot of a group the column leaves free
-        for (int cc = 0; cc < grp[gq].y; ++cc) {
-            uint16_t *cell = idx + (size_t)grp[gq].x + (size_t)cc * 32 + lane0;
-            bool taken[8] = {false};
-            for (int p = 0; p < 8; ++p)
-                if (cell[p] != kNoSlot) taken[bank_group(cell[p])] = true;
-            int k = 0;
+        build_quarters(set_p);
+        hp.n_grp_p = (int32_t)(quarters.size() / 4);
+        build_quarters(set_a);
+        hp.n_grp_a = (int32_t)(quarters.size() / 4);
+        build_quarters(set_b);
+        const int32_t n_grp = (int32_t)(quarters.size() / 4);
+        hp.n_grp = n_grp;
+        std::vector<int2> grp(n_grp);
+        int64_t total = 0;
+        for (int32_t gq = 0; gq < n_grp; ++gq) {
+            const int cols = quarters[(size_t)gq * 4].delta;  // sorted: the first is the widest
+            grp[gq] = make_int2((int32_t)total, cols);
+            total += 32 * (int64_t)cols;
+            if (total > (int64_t)1 << 24) return false;
+        }
+        auto al16 = [](int64_t x) { return (x + 15) & ~(int64_t)15; };
+        const int64_t off_row = al16((int64_t)sizeof(int2) * n_grp);
+        const int64_t off_idx = al16(off_row + 2 * 32 * (int64_t)n_grp);
+        const int64_t bytes = al16(off_idx + 2 * total);
+        if (bytes > INT32_MAX / 2) return false;
+        hp.off_row = (int32_t)off_row;
+        hp.off_idx = (int32_t)off_idx;
+        hp.tab.assign((size_t)bytes, 0);
+        memcpy(hp.tab.data(), grp.data(), sizeof(int2) * n_grp);
+        uint16_t *row = reinterpret_cast<uint16_t *>(hp.tab.data() + off_row);
+        uint16_t *idx = reinterpret_cast<uint16_t *>(hp.tab.data() + off_idx);
+        std::fill(row, row + 32 * (size_t)n_grp, kNoSlot);
+        std::fill(idx, idx + total, kNoSlot);
+        std::vector<std::pair<int, int>> edges;
+        std::vector<uint16_t> eslot;
+        for (size_t qi = 0; qi < quarters.size(); ++qi) {
+            const Quarter &q = quarters[qi];
+            const int32_t gq = (int32_t)(qi / 4), lane0 = 8 * (int32_t)(qi % 4);
+            edges.clear();
+            eslot.clear();
             for (int p = 0; p < 8; ++p) {
-                if (cell[p] != kNoSlot) continue;
-                while (k < 7 && taken[k]) ++k;
-                cell[p] = (uint16_t)(zbase + k);
+                if (q.row[p] < 0) continue;
+                // output id: the parity index, or the coded row
+                row[(size_t)gq * 32 + lane0 + p] = (uint16_t)(q.row[p] < mp ? q.row[p] / ks : q.row[p] - mp);
+                for (uint16_t sl : in[q.row[p]]) {
+                    edges.emplace_back(p, bank_group(sl));
+                    eslot.push_back(sl);
+                }
+            }
+            const std::vector<int> col = colour_edges(edges, std::max(q.delta, 1));
+            for (size_t e = 0; e < edges.size(); ++e)
+                idx[(size_t)grp[gq].x + (size_t)col[e] * 32 + lane0 + edges[e].first] = eslot[e];
+            // empty cells of each column: the zero slot of a group the column leaves free
+            for (int cc = 0; cc < grp[gq].y; ++cc) {
+                uint16_t *cell = idx + (size_t)grp[gq].x + (size_t)cc * 32 + lane0;
+                bool taken[8] = {false};
+                for (int p = 0; p < 8; ++p)
+                    if (cell[p] != kNoSlot) taken[bank_group(cell[p])] = true;
+                int k = 0;
+                for (int p = 0; p < 8; ++p) {
+                    if (cell[p] != kNoSlot) continue;
+                    while (k < 7 && taken[k]) ++k;
+                    cell[p] = (uint16_t)(zbase + k);
+                }
             }
         }
-    }
+        return true;
+    };
 
-    cudaError_t e = cudaMalloc(&c->sl_tab, (size_t)bytes);
-    if (e == cudaSuccess) e = cudaMemcpy(c->sl_tab, tab.data(), (size_t)bytes, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return e;
+    // as few parts as let every part run with two slot buffers of 16 bytes;
+    // one part with one buffer when no split up to kSliceParts does
+    const size_t budget = c->smem_optin;
+    // the same rule as the batch layout: tables rounded to 256 bytes, then the buffers
+    auto fits = [&](const HostPart &hp, int nbuf) {
+        return (size_t)nbuf * (size_t)slots * 16 + ((hp.tab.size() + 255) & ~(size_t)255) + kSlotAlign <=
+               budget;
+    };
+    std::vector<HostPart> parts;
+    for (int P = 1; P <= kSliceParts && parts.empty(); ++P) {
+        // coded rows into P ranges of about equal entries
+        std::vector<int32_t> cut(P + 1, n);
+        cut[0] = 0;
+        const int64_t per = ((int64_t)con_ptr[n] + P - 1) / P;
+        for (int q = 1, r = 0; q < P; ++q) {
+            while (r < n && con_ptr[r] < per * q) ++r;
+            cut[q] = r;
+        }
+        std::vector<HostPart> cand(P);
+        bool ok = true;
+        for (int q = 0; q < P && ok; ++q) ok = make_part(cut[q], cut[q + 1], cand[q]) && fits(cand[q], 2);
+        if (ok) parts = std::move(cand);
+    }
+    if (parts.empty()) {  // one part, one buffer
+        HostPart hp;
+        if (!make_part(0, n, hp) || !fits(hp, 1)) return cudaSuccess;
+        parts.push_back(std::move(hp));
+    }
+    for (size_t q = 0; q < parts.size(); ++q) {
+        SlicePart &sp = c->sl_part[q];
+        const HostPart &hp = parts[q];
+        cudaError_t e = cudaMalloc(&sp.tab, hp.tab.size());
+        if (e == cudaSuccess) e = cudaMemcpy(sp.tab, hp.tab.data(), hp.tab.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+        sp.tab_bytes = (int32_t)hp.tab.size();
+        sp.n_grp = hp.n_grp;
+        sp.n_grp_p = hp.n_grp_p;
+        sp.n_grp_a = hp.n_grp_a;
+        sp.off_row = hp.off_row;
+        sp.off_idx = hp.off_idx;
+    }
+    c->sl_parts = (int32_t)parts.size();
     c->sl_box_rows = box_rows;
     c->sl_bpad = (int32_t)bpad;
-    c->sl_n_grp = n_grp;
-    c->sl_n_grp_p = n_grp_p;
-    c->sl_n_grp_a = n_grp_a;
-    c->sl_tab_bytes = (int32_t)bytes;
-    c->sl_off_row = (int32_t)off_row;
-    c->sl_off_idx = (int32_t)off_idx;
     c->sl_zbase = (int32_t)zbase;
     c->sl_slots = (int32_t)slots;
     return cudaSuccess;
 }
 
-void free_slice_tables(fs_code *c) { cudaFree(c->sl_tab); }
+void free_slice_tables(fs_code *c) {
+    for (int q = 0; q < kSliceParts; ++q) cudaFree(c->sl_part[q].tab);
+}
 
 namespace {
 
@@ -866,8 +919,8 @@ namespace {
 // two buffers when they fit.
 // The launch arguments of a code's slice encode with v words per slot and
 // nbuf buffers; false when no tensor map can be made.
-bool slice_setup(const fs_code *c, const void *data, void *parity, void *coded, int v, int nbuf,
-                 SliceArgs *a, CUtensorMap *map) {
+bool slice_setup(const fs_code *c, int part, const void *data, void *parity, void *coded, int v,
+                 int nbuf, SliceArgs *a, CUtensorMap *map) {
     EncodeTiledFn encode = tensor_map_encoder();
     if (!encode) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)c->t, (cuuint64_t)c->b};
@@ -879,16 +932,18 @@ bool slice_setup(const fs_code *c, const void *data, void *parity, void *coded, 
                v == 2 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
-    a->tab = reinterpret_cast<const uint4 *>(c->sl_tab);
-    a->tab_words = c->sl_tab_bytes / 16;
-    a->off_row = c->sl_off_row;
-    a->off_idx = c->sl_off_idx;
+    const SlicePart &sp = c->sl_part[part];
+    a->tab = reinterpret_cast<const uint4 *>(sp.tab);
+    a->tab_words = sp.tab_bytes / 16;
+    a->off_row = sp.off_row;
+    a->off_idx = sp.off_idx;
+    a->write_parity = part == 0 ? 1 : 0;
     a->parity = static_cast<uint4 *>(parity);
     a->coded = static_cast<uint4 *>(coded);
     a->m = c->m;
-    a->n_grp = c->sl_n_grp;
-    a->n_grp_p = c->sl_n_grp_p;
-    a->n_grp_a = c->sl_n_grp_a;
+    a->n_grp = sp.n_grp;
+    a->n_grp_p = sp.n_grp_p;
+    a->n_grp_a = sp.n_grp_a;
     a->bpad = c->sl_bpad;
     a->zbase = c->sl_zbase;
     a->slots = c->sl_slots;
@@ -907,24 +962,38 @@ bool slice_setup(const fs_code *c, const void *data, void *parity, void *coded, 
 // arithmetic) matter more than the slot width, so: 32-byte slots (full-sector
 // copies and stores) when two buffers of them fit, else 16-byte slots, with
 // two buffers when they fit.
+// Whether the automatic policy picks slices for c: a code whose tables fit in
+// one part always (each input byte crosses DRAM once); a code split into
+// parts only for blocks up to 16 KiB, because every part re-reads the data
+// and, for the long rows such codes have, the shared-memory gathers then cost
+// as much as the row-gather encode at large blocks (measured).
+bool slices_pay(const fs_code *c) {
+    if (c->sl_slots == 0 || c->t >= ((int64_t)1 << 31)) return false;
+    return c->encode_slices >= 2 || c->sl_parts == 1 || c->t <= 16384;
+}
+
 bool launch_slices(const fs_code *c, const void *data, void *parity, void *coded, int32_t *hdr,
                    cudaStream_t s, cudaError_t *err) {
     *err = cudaSuccess;
-    if (!c->encode_slices || c->sl_slots == 0 || c->t >= ((int64_t)1 << 31)) return false;
+    if (!c->encode_slices || !slices_pay(c)) return false;
     int v = c->encode_slices == 2   ? 1
             : c->encode_slices == 3 ? 2
             : (slice_smem_bytes(c, 2, 2) <= c->smem_optin && c->tw >= 2 ? 2 : 1);
     if (slice_smem_bytes(c, v, 1) > c->smem_optin) v = 1;
     const int nbuf = slice_smem_bytes(c, v, 2) <= c->smem_optin ? 2 : 1;
     const size_t smem = slice_smem_bytes(c, v, nbuf);
-    CUtensorMap map;
-    SliceArgs a;
-    if (!slice_setup(c, data, parity, coded, v, nbuf, &a, &map)) return false;
-    a.ticket = hdr + WS_COUNT_A;
-    a.status = hdr + WS_STATUS;
     auto kern = v == 2 ? k_slices<2> : k_slices<1>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) {
+    for (int q = 0; q < c->sl_parts && e == cudaSuccess; ++q) {  // one launch per part
+        CUtensorMap map;
+        SliceArgs a;
+        if (!slice_setup(c, q, data, parity, coded, v, nbuf, &a, &map)) {
+            if (q == 0) return false;
+            e = cudaErrorInvalidValue;
+            break;
+        }
+        a.ticket = hdr + WS_ENC_TICKETS + q;
+        a.status = hdr + WS_STATUS;
         // one CTA per SM but one: each CTA fills its SM's shared memory, so a
         // one-CTA decoding schedule launched beside the encode on another
         // stream would otherwise wait for the whole encode
@@ -1001,7 +1070,6 @@ struct EncodeBatch {
     CUtensorMap *d_maps = nullptr;
     int4 *d_items = nullptr;
     int n_items = 0;
-    int32_t max_slots = 0;
     size_t smem_sl = 0;
     int32_t *d_ctr = nullptr;     // ticket counters (precode, LT), item counter, status
     int num_sms = 1, ctas = 1;
@@ -1021,20 +1089,26 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
     // batch slice kernel; the layout of a launch is the largest buffers and
     // the largest tables of its stripes, so stripes are added while that fits
     const size_t budget = n > 0 ? codes[0]->smem_optin : 0;
+    auto tab_of = [&](int32_t i) {
+        int32_t t = 0;
+        for (int q = 0; q < codes[i]->sl_parts; ++q) t = std::max(t, codes[i]->sl_part[q].tab_bytes);
+        return t;
+    };
     std::vector<int32_t> order;
+    // (in a batch only single-part codes: beside many other stripes the
+    // row-gather kernel overlaps the large ones better than a split would)
     for (int32_t i = 0; i < n; ++i)
-        if (codes[i]->encode_slices && codes[i]->sl_slots > 0 && codes[i]->t < ((int64_t)1 << 31))
+        if (codes[i]->encode_slices && slices_pay(codes[i]) && codes[i]->sl_parts == 1)
             order.push_back(i);
-    std::sort(order.begin(), order.end(),
-              [&](int32_t x, int32_t y) { return codes[x]->sl_tab_bytes < codes[y]->sl_tab_bytes; });
+    std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return tab_of(x) < tab_of(y); });
+    // every stripe lays out its own tables and two buffers, so a stripe
+    // qualifies when its own layout fits
     std::vector<char> sliced(n, 0);
-    int32_t max_slots = 0, max_tab = 0;
+    size_t smem_sl = 0;
     for (int32_t i : order) {
-        const int32_t ms = std::max(max_slots, codes[i]->sl_slots);
-        const int32_t mt = std::max(max_tab, codes[i]->sl_tab_bytes);
-        if ((size_t)2 * ms * 16 + (size_t)mt + kSlotAlign > budget) continue;
-        max_slots = ms;
-        max_tab = mt;
+        const size_t need = (size_t)2 * codes[i]->sl_slots * 16 + (((size_t)tab_of(i) + 255) & ~(size_t)255) + kSlotAlign;
+        if (need > budget) continue;
+        smem_sl = std::max(smem_sl, need);
         sliced[i] = 1;
     }
     std::vector<SliceArgs> sl;
@@ -1043,16 +1117,16 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
     constexpr int32_t kItemSlices = 32;
     for (int32_t i = 0; i < n; ++i) {
         if (!sliced[i]) continue;
-        SliceArgs a;
-        CUtensorMap map;
-        if (!slice_setup(codes[i], data[i], parity[i], coded[i], 1, 2, &a, &map)) {
-            sliced[i] = 0;
-            continue;
+        for (int q = 0; q < codes[i]->sl_parts; ++q) {  // every part of the stripe
+            SliceArgs a;
+            CUtensorMap map;
+            if (!slice_setup(codes[i], q, data[i], parity[i], coded[i], 1, 2, &a, &map))
+                return cudaErrorInvalidValue;
+            for (int32_t s0 = 0; s0 < a.n_slices; s0 += kItemSlices)
+                items.push_back(make_int4((int)sl.size(), s0, std::min(a.n_slices, s0 + kItemSlices), 0));
+            sl.push_back(a);
+            maps.push_back(map);
         }
-        for (int32_t s0 = 0; s0 < a.n_slices; s0 += kItemSlices)
-            items.push_back(make_int4((int)sl.size(), s0, std::min(a.n_slices, s0 + kItemSlices), 0));
-        sl.push_back(a);
-        maps.push_back(map);
     }
     for (int32_t i = 0; i < n; ++i) {
         if (sliced[i]) continue;
@@ -1101,8 +1175,7 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
     b->ctas = n > 0 ? std::min(codes[0]->gather_ctas, kCtasPerSm) : 1;
     const int32_t zero[4] = {0, 0, 0, 0};
     b->n_items = (int)items.size();
-    b->max_slots = max_slots;
-    b->smem_sl = (size_t)2 * max_slots * 16 + (size_t)max_tab + kSlotAlign;
+    b->smem_sl = smem_sl;
     cudaError_t e = plan_upload(&b->d_ctr, zero, 4);
     if (e == cudaSuccess) e = plan_upload(&b->d_pre, pre.data(), pre.size());
     if (e == cudaSuccess) e = plan_upload(&b->d_lt, lt.data(), lt.size());
@@ -1125,7 +1198,7 @@ cudaError_t encode_batch_run(const EncodeBatch *b, cudaStream_t s) {
     if (e == cudaSuccess && b->n_items > 0) {
         const int g = b->n_items < b->num_sms ? b->n_items : b->num_sms;
         k_slices_batch<<<g, kSliceThreads, b->smem_sl, s>>>(b->d_sl, b->d_maps, b->d_items, b->n_items,
-                                                           b->max_slots, b->d_ctr + 2, b->d_ctr + 3);
+                                                           b->d_ctr + 2, b->d_ctr + 3);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && b->t_pre > 0) {

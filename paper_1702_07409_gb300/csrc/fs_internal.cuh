@@ -13,6 +13,22 @@
 // checks): constraint g < n is coded row g with payload c_g; constraint
 // n + j is precode check j with payload zero and vars = members + {b + j}.
 // The LT graph is the prefix con_ptr[0..n], con_idx[0..e_lt).
+// Tables of one part of a code's slice encode (see fs_code::sl_part): one
+// device array the kernel copies to shared memory, each piece 16-byte aligned:
+//   grp   int2 [n_grp]       {first entry, columns of the group}
+//   row   uint16 [32 n_grp]  output row of each lane (parity index or coded
+//                            row), 0xFFFF pad
+//   idx   uint16 [...]       group entries, column-major (32 lanes)
+// The first n_grp_p groups are precode (parity) rows, groups up to n_grp_a
+// coded rows that read no parity, the rest coded rows that read one.
+constexpr int kSliceParts = 4;
+struct SlicePart {
+    unsigned char *tab = nullptr;
+    int32_t tab_bytes = 0;  // multiple of 16
+    int32_t n_grp = 0, n_grp_p = 0, n_grp_a = 0;
+    int32_t off_row = 0, off_idx = 0;  // byte offsets
+};
+
 struct fs_code {
     int32_t b, m, n, k_int, n_con;
     int64_t t;            // block bytes
@@ -44,23 +60,15 @@ struct fs_code {
     int rows_per_ticket;  // coded rows per work ticket of the row-gather encode (1..16)
     // slice encode tables (present when sl_slots > 0): every input block has
     // a 16-byte shared-memory slot per byte slice; data block v is slot v,
-    // parity j is slot sl_bpad + j
+    // parity j is slot sl_bpad + j. The coded rows are split into sl_parts
+    // parts (each with the parity rows too) so that every part's tables fit
+    // shared memory beside the slot buffers; each part reads the data again.
     int32_t sl_box_rows;  // rows of one TMA box (data blocks per copy)
     int32_t sl_bpad;      // data slots, b rounded up to sl_box_rows
     int32_t sl_zbase;     // first of 8 zero slots (one per bank group), after the parities
     int32_t sl_slots;     // slots of one buffer (sl_zbase + 8)
-    int32_t sl_n_grp;     // warp groups of 32 output rows
-    int32_t sl_n_grp_p;   // the first sl_n_grp_p groups are precode (parity) rows,
-    int32_t sl_n_grp_a;   // groups up to sl_n_grp_a coded rows that read no parity
-    // one device array holding the tables the kernel copies to shared
-    // memory, each part starting on a 16-byte boundary:
-    //   grp   int2 [sl_n_grp]       {first entry, columns of the group}
-    //   row   uint16 [32 sl_n_grp]  output row of each lane (parity index or
-    //                               coded row), 0xFFFF pad
-    //   idx   uint16 [...]          group entries, column-major (32 lanes)
-    unsigned char *sl_tab;
-    int32_t sl_tab_bytes;  // multiple of 16
-    int32_t sl_off_row, sl_off_idx;  // byte offsets
+    int32_t sl_parts;     // parts (1..kSliceParts)
+    SlicePart sl_part[kSliceParts];
 };
 
 // Builds the slice encode tables of c (host arrays of the joint graph);
@@ -119,6 +127,7 @@ enum {
     WS_COUNT_B = 5,
     WS_TILE_CTR = 6,
     WS_STAGED = 7,      // 1: every level fits the payload kernel's shared-memory stages
+    WS_ENC_TICKETS = 16,  // encode: ticket counters of the slice launches (one per part)
     WS_HDR_BYTES = 256
 };
 

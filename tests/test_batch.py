@@ -21,6 +21,7 @@ SHAPES = [
     (2000, 64, 2600, 1024, gen.DIST_FINITE40, 0.0, 0.0),
     (90, 0, 117, 16384, gen.DIST_RSD, 0.05, 0.01),
     (512, 16, 700, 256, gen.DIST_FINITE40, 0.0, 0.0),
+    (4096, 0, 5325, 1024, gen.DIST_RSD, 0.05, 0.01),  # slice tables in several parts
 ]
 
 

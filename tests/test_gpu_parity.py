@@ -329,3 +329,18 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     _, _, cd = case.encode_gpu()
     _, want = oracle.encode(case.g, case.data, case.t)
     assert np.array_equal(_host(cd), want)
+
+
+@pytest.mark.parametrize("t", [1024, 4096 + 16])
+def test_large_code_encodes_in_parts(t):
+    """A code whose slice tables do not fit beside two slot buffers (RSD
+    k=4096, n=5325: ~190 KB of tables) is encoded in several parts, each
+    reading the data again; the result is the oracle's."""
+    case = Case(4096, 0, 5325, t, gen.DIST_RSD, 0.05, 0.01)
+    _, _, cd = case.encode_gpu()
+    _, want = oracle.encode(case.g, case.data, t)
+    assert np.array_equal(_host(cd), want)
+    pre = Case(3000, 96, 4000, 2048, gen.DIST_RSD, 0.05, 0.01)  # parts with parities
+    _, p, cd = pre.encode_gpu()
+    par, cod = oracle.encode(pre.g, pre.data, pre.t)
+    assert np.array_equal(_host(cd), cod) and np.array_equal(_host(p), par)
