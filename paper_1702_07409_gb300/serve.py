@@ -136,6 +136,16 @@ class Server:
     def submit(self, r: Request):
         self.waiting.append(r)
 
+    def cancel(self, rid: int) -> bool:
+        """Withdraws a request that has not been admitted yet (an admitted
+        one runs to its end). Returns whether it was withdrawn."""
+        for r in self.waiting:
+            if r.rid == rid:
+                self.waiting.remove(r)
+                r.out["cancelled"] = True
+                return True
+        return False
+
     def pump(self, now: float) -> None:
         """Retires finished waves, then admits arrived requests (FIFO) into
         one wave and enqueues it."""
@@ -154,6 +164,10 @@ class Server:
                 r.out["dropped"] = True
                 continue
             need = self._need(r)
+            if need > self.budget:  # can never fit: reject it without evicting anything
+                r.done = now
+                r.out["rejected"] = True
+                continue
             target = self.stripes.get(r.target) if r.kind != "encode" else None
             if target is not None:
                 target.busy = True  # never evict the stripe this request works on

@@ -82,3 +82,36 @@ def test_decode_recovers_the_stripe_data():
     un = reqs[0].out["unrecovered"].bool()
     assert torch.equal(out[~un], data[~un]) and bool((out[un] == 0).all())
     srv.close()
+
+
+def test_budget_eviction_rejection_and_cancel():
+    """Admission under a small budget: resident stripes are evicted least
+    recently used first, a later request on an evicted stripe is dropped, a
+    request larger than the whole budget is rejected (not left waiting), a
+    waiting request can be withdrawn, and the budget is never exceeded."""
+    import torch
+    from paper_1702_07409_gb300.serve import Request, Server
+    k, t = 64, 4096
+    stripe_bytes = (k + round(k * 1.3)) * t
+    srv = Server(int(3.5 * stripe_bytes), streams=2)
+    for i in range(3):
+        srv.add_resident(i, k=k, t=t, seed=20 + i)
+    assert list(srv.stripes) == [0, 1, 2]
+    # a new stripe needs room: the least recently used (0) goes
+    srv.run([Request(0, "encode", 0.0, k=k, t=t, target=10, seed=99)], realtime=False)
+    assert 0 not in srv.stripes and 10 in srv.stripes and srv.evictions == 1
+    # a decode of the evicted stripe is dropped, one of a resident stripe is served
+    reqs = srv.run([Request(1, "decode", 0.0, target=0, seed=5, erase_frac=0.1),
+                    Request(2, "decode", 0.0, target=1, seed=6, erase_frac=0.1)], realtime=False)
+    assert reqs[0].out.get("dropped") and not reqs[1].out.get("dropped")
+    # larger than the whole budget: rejected
+    before = set(srv.stripes)
+    big = srv.run([Request(3, "encode", 0.0, k=4096, t=65536, target=11, seed=7)], realtime=False)
+    assert big[0].out.get("rejected") and 11 not in srv.stripes
+    assert set(srv.stripes) == before  # nothing evicted for it
+    # withdrawn before admission
+    srv.submit(Request(4, "decode", 0.0, target=2, seed=8, erase_frac=0.1))
+    assert srv.cancel(4) and not srv.cancel(4) and not srv.waiting
+    torch.cuda.synchronize()
+    assert srv.peak <= srv.budget
+    srv.close()
