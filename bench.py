@@ -685,6 +685,9 @@ def run_serving(args):
         for size in sizes:  # every code the stream can ask for, built before the clock starts
             for t in (16384, 65536):
                 srv.code_for(size // t, t)
+        # every kernel loaded before the clock starts: the smallest and the
+        # largest code of the stream (their decodes take different kernels)
+        srv.warm_up(((sizes[0] // 65536, 65536), (sizes[-1] // 16384, 16384)))
         meta = {}
         prng = np.random.default_rng(77 + rank)
         for p in range(args.pool):
@@ -707,6 +710,7 @@ def run_serving(args):
                 bytes_ += int(r.out["data_out"].numel())
         span = max(r.done for r in served) if served else wall
         res = dict(latency_stats(reqs), gbs=round(bytes_ / span / 1e9, 2), span_s=round(span, 3),
+                   wave_stats=srv.wave_stats(),
                    waves=srv.n_waves, peak_gb=round(srv.peak / 1e9, 2), evictions=srv.evictions,
                    dropped=sum(1 for r in reqs if r.out.get("dropped")),
                    rejected=sum(1 for r in reqs if r.out.get("rejected")))

@@ -91,6 +91,9 @@ class Server:
         self.evictions = 0
         self.encoding = set()  # stripes whose encode is in flight
         self.n_waves = 0
+        self.wave_log = []
+        self.t_host0 = time.perf_counter()
+        self._pinned = []
 
     # -- codes and memory --------------------------------------------------
     def code_for(self, k: int, t: int):
@@ -132,6 +135,27 @@ class Server:
         self.waiting.append(r)
         self.pump(0.0)
         self.drain()
+
+    def warm_up(self, shapes=((64, 16384),)) -> None:
+        """Runs one request of each kind on a scratch stripe of each (k, t) in
+        shapes, then removes the stripes. A kernel's
+        module is loaded on its first launch, and a load that meets a busy
+        device holds the host until that work ends (seconds, behind a full
+        wave), so every kernel a wave can launch, the library's and torch's,
+        is launched once here before serving starts."""
+        for j, (k, t) in enumerate(shapes):
+            sid = -(1 << 30) - j
+            for r in (Request(-1, "encode", 0.0, k=k, t=t, target=sid, seed=1 + j),
+                      Request(-2, "decode", 0.0, target=sid, seed=2 + j, erase_frac=0.1),
+                      Request(-3, "update", 0.0, target=sid, seed=3 + j, n_update=1),
+                      Request(-4, "repair", 0.0, target=sid, seed=4 + j, n_lost=1)):
+                self.waiting.append(r)
+                self.pump(0.0)
+                self.drain()
+            st = self.stripes.pop(sid, None)
+            if st is not None:
+                self.resident -= st.nbytes
+        self.peak = self.resident + self.transient
 
     def submit(self, r: Request):
         self.waiting.append(r)
@@ -188,14 +212,29 @@ class Server:
         if wave:
             self._launch(wave)
 
+    def _upload(self, a: np.ndarray):
+        """Host array to the device without blocking the host: through pinned
+        memory, so the copy is queued on the current stream (a copy from
+        pageable memory would first wait for that stream's earlier work). The
+        pinned buffer is kept until the wave ends."""
+        torch = self.torch
+        h = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        d = h.to(self.device, non_blocking=True)
+        self._pinned.append(h)
+        return d
+
     def _launch(self, wave):
         torch = self.torch
+        h0 = time.perf_counter()
+        self._pinned = []
         s = self.streams[self.next_stream]
         self.next_stream = (self.next_stream + 1) % len(self.streams)
         batches = []
         with torch.cuda.stream(s):
             encs = [r for r in wave if r.kind == "encode"]
             decs = [r for r in wave if r.kind == "decode"]
+            tp = {}
+            t_a = time.perf_counter()
             if encs:
                 items = []
                 for r in encs:
@@ -207,16 +246,20 @@ class Server:
                     coded = torch.empty((n, r.t), dtype=torch.uint8, device=self.device)
                     r.out["stripe"] = _Stripe(r.target, code, r.k, n, r.t, data, coded)
                     items.append({"code": code, "data": data, "coded": coded})
+                t_b = time.perf_counter()
                 b = fs.Batch(items, fs.OP_ENCODE)
+                t_c = time.perf_counter()
                 b.run(s)
                 batches.append(b)
+                tp.update(enc_inputs=t_b - t_a, enc_plan=t_c - t_b, enc_run=time.perf_counter() - t_c)
+            t_a = time.perf_counter()
             if decs:
                 items = []
                 for r in decs:
                     st = self.stripes[r.target]
                     er = np.zeros(st.n, np.uint8)
                     er[gen.sample_indices(st.n, gen.round_count(r.erase_frac, st.n), r.seed)] = 1
-                    r.out.update(erased=torch.from_numpy(er).to(self.device, non_blocking=True),
+                    r.out.update(erased=self._upload(er),
                                  data_out=torch.empty((st.k, st.t), dtype=torch.uint8, device=self.device),
                                  unrecovered=torch.empty(st.k, dtype=torch.uint8, device=self.device),
                                  n_unrecovered=torch.empty(1, dtype=torch.int32, device=self.device),
@@ -224,9 +267,13 @@ class Server:
                     items.append({"code": st.code, "coded": st.coded, "erased": r.out["erased"],
                                   "data_out": r.out["data_out"], "unrecovered": r.out["unrecovered"],
                                   "n_unrecovered": r.out["n_unrecovered"], "ws": r.out["ws"]})
+                t_b = time.perf_counter()
                 b = fs.Batch(items, fs.OP_DECODE)
+                t_c = time.perf_counter()
                 b.run(s)
                 batches.append(b)
+                tp.update(dec_inputs=t_b - t_a, dec_plan=t_c - t_b, dec_run=time.perf_counter() - t_c)
+            t_a = time.perf_counter()
             for r in wave:
                 if r.kind == "update":
                     st = self.stripes[r.target]
@@ -235,22 +282,31 @@ class Server:
                     g.manual_seed(r.seed)
                     new = torch.randint(0, 256, (r.n_update, st.t), dtype=torch.uint8,
                                         device=self.device, generator=g)
-                    d_idx = torch.from_numpy(idx).to(self.device, non_blocking=True)
+                    d_idx = self._upload(idx)
                     ws = st.code.workspace(fs.OP_UPDATE, r.n_update, device=self.device)
                     st.code.update(d_idx, r.n_update, new, st.data, None, st.coded, ws, stream=s)
                     r.out.update(idx=d_idx, new=new, ws=ws)
                 elif r.kind == "repair":
                     st = self.stripes[r.target]
                     lost = gen.sample_indices(st.n, r.n_lost, r.seed)
-                    d_lost = torch.from_numpy(lost).to(self.device, non_blocking=True)
+                    d_lost = self._upload(lost)
                     ws = st.code.workspace(fs.OP_REPAIR, device=self.device)
-                    st.coded[d_lost.long()] = 0  # the lost blocks are gone
+                    # the lost blocks are gone; index_fill_ takes the value as a kernel
+                    # argument (an indexed assignment of a Python scalar copies it from
+                    # pageable memory, which waits for the stream's queued work)
+                    st.coded.index_fill_(0, d_lost.long(), 0)
                     st.code.repair(d_lost, r.n_lost, st.data, None, st.coded, ws, stream=s)
                     r.out.update(lost=d_lost, ws=ws)
+            tp["upd_rep"] = time.perf_counter() - t_a
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(s)
-        self.waves.append((ev, wave, sum(r.out["need"] for r in wave), batches))
+        self.waves.append((ev, wave, sum(r.out["need"] for r in wave), batches + self._pinned))
         self.n_waves += 1
+        # server counters: what the wave held and how long the host took to launch it
+        kinds = collections.Counter(r.kind for r in wave)
+        self.wave_log.append({"n": len(wave), "kinds": dict(kinds), "host_ms": (time.perf_counter() - h0) * 1e3,
+                              "phases_ms": {k: v * 1e3 for k, v in tp.items()},
+                              "event": ev, "launched": time.perf_counter() - self.t_host0})
 
     def _retire(self, block: bool = False):
         keep = []
@@ -275,7 +331,7 @@ class Server:
                     if st is not None:
                         st.busy = False
                         self.stripes.move_to_end(r.target)
-            self.retired.extend(batches)
+            self.retired.extend(b for b in batches if isinstance(b, fs.Batch))
         self.waves = keep
 
     def drain(self):
@@ -289,9 +345,12 @@ class Server:
         torch = self.torch
         reqs = sorted(requests, key=lambda r: r.arrival)
         torch.cuda.synchronize()
+        self.wave_log = []
+        self.n_waves = 0
         self.t0_event = torch.cuda.Event(enable_timing=True)
         self.t0_event.record()
         t0 = time.perf_counter()
+        self.t_host0 = t0
         i = 0
         while i < len(reqs) or self.waiting or self.waves:
             now = time.perf_counter() - t0 if realtime else float("inf")
@@ -312,6 +371,24 @@ class Server:
                 r.out["rejected"] = True
         self.drain()
         return reqs
+
+    def wave_stats(self) -> dict:
+        """Summary of the waves of the last run: sizes, host launch time, and
+        the device time from one wave's end to the next's (work per wave)."""
+        if not self.wave_log:
+            return {}
+        ends = sorted(self.t0_event.elapsed_time(w["event"]) for w in self.wave_log if w["event"].query())
+        gaps = np.diff([0.0] + ends)
+        n = np.array([w["n"] for w in self.wave_log])
+        host = np.array([w["host_ms"] for w in self.wave_log])
+        phases = collections.Counter()
+        for w in self.wave_log:
+            phases.update(w.get("phases_ms", {}))
+        return {"waves": len(self.wave_log), "mean_requests": round(float(n.mean()), 2),
+                "host_ms_by_phase": {k: round(v, 1) for k, v in phases.items()},
+                "max_requests": int(n.max()), "host_ms_per_wave": round(float(host.mean()), 3),
+                "host_ms_total": round(float(host.sum()), 1),
+                "device_ms_between_wave_ends": round(float(np.median(gaps)), 3)}
 
     def close(self):
         self.drain()

@@ -70,10 +70,13 @@ def test_mixed_equals_alone_and_budget_holds():
 
 def test_decode_recovers_the_stripe_data():
     """A decode of a stripe with 10% erased returns its data (recovered
-    blocks) and zeros (unrecovered ones)."""
+    blocks) and zeros (unrecovered ones). The warm-up before it leaves no
+    stripe and no bytes behind."""
     import torch
     from paper_1702_07409_gb300.serve import Request, Server
     srv = Server(1 << 30, streams=2)
+    srv.warm_up(((32, 1024), (300, 64)))
+    assert not srv.stripes and srv.resident == 0 and srv.transient == 0 and not srv.waiting
     srv.add_resident(0, k=128, t=4096, seed=5)
     data = srv.stripes[0].data.clone()
     reqs = srv.run([Request(0, "decode", 0.0, target=0, seed=9, erase_frac=0.1)], realtime=False)
