@@ -127,6 +127,16 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
  *                        fewer rows per ticket keep the tickets in flight on a
  *                        narrower byte range of every block (better L2 reuse
  *                        of the gathered inputs) at more scheduling cost
+ *   FS_TUNE_PEEL_COLUMNS 1: the payload of a decode holds one 16-byte
+ *                        column of every intermediate in shared memory and
+ *                        walks all levels there, when the code fits (k_int + 1
+ *                        16-byte slots: about 13500 intermediates); it moves
+ *                        only the algorithmic bytes, in 16-byte pieces.
+ *                        0 (default): the slice payload, which gathers
+ *                        recovered blocks through L2 and HBM. Its plan is made
+ *                        by the decoding schedule: set the knob before
+ *                        fs_decode / fs_decode_schedule (a payload without
+ *                        the plan reports FS_ERR_INVALID in the workspace)
  * Returns FS_ERR_INVALID for an unknown knob or an out-of-range value. Not
  * thread-safe against concurrent hot calls on the same code. */
 #define FS_TUNE_PEEL_CTAS   1
@@ -135,6 +145,7 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
 #define FS_TUNE_L2_HINTS    4
 #define FS_TUNE_ENCODE_SLICES 5
 #define FS_TUNE_ROWS_PER_TICKET 6
+#define FS_TUNE_PEEL_COLUMNS 7
 fs_status fs_code_set_tuning(fs_code *code, int knob, int value);
 
 /* Bytes of caller-provided device workspace that op needs. n_items is the

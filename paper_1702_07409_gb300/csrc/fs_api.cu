@@ -165,6 +165,7 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     c->l2_hints = 0;
     c->encode_slices = 1;
     c->rows_per_ticket = 16;
+    c->peel_columns = 0;
     cudaError_t e = cudaGetDevice(&c->device);
     int v = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c->device);
@@ -232,6 +233,10 @@ FS_API fs_status fs_code_set_tuning(fs_code *c, int knob, int value) {
         case FS_TUNE_GATHER_CTAS:
             if (value < 1 || value > 16) return FS_ERR_INVALID;
             c->gather_ctas = value;
+            return FS_OK;
+        case FS_TUNE_PEEL_COLUMNS:
+            if (value != 0 && value != 1) return FS_ERR_INVALID;
+            c->peel_columns = value;
             return FS_OK;
     }
     return FS_ERR_INVALID;

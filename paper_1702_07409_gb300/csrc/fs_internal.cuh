@@ -58,6 +58,8 @@ struct fs_code {
     int l2_hints;         // 1: L2 evict-last / evict-first hints on the gathers
     int encode_slices;    // 1: shared-memory slice encode when the code fits
     int rows_per_ticket;  // coded rows per work ticket of the row-gather encode (1..16)
+    int peel_columns;     // 1: column payload (every intermediate of a byte column in
+                          // shared memory) when the code fits it; 0 (default): slice payload
     // slice encode tables (present when sl_slots > 0): every input block has
     // a 16-byte shared-memory slot per byte slice; data block v is slot v,
     // parity j is slot sl_bpad + j. The coded rows are split into sl_parts
@@ -113,6 +115,8 @@ void decode_batch_free(DecodeBatch *b);
 void free_slice_tables(fs_code *c);
 
 constexpr int kRecipeSeg = 8;  // recipe entries one payload thread gathers at once
+constexpr int kColSegEntries = 7;  // row positions of one column-payload segment record
+constexpr int kColSegMax = 256;    // segments of one column-payload step (one per thread)
 
 // ---- workspace layouts (byte offsets from d_ws, 256-aligned) --------------
 static inline size_t fs_align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -127,6 +131,7 @@ enum {
     WS_COUNT_B = 5,
     WS_TILE_CTR = 6,
     WS_STAGED = 7,      // 1: every level fits the payload kernel's shared-memory stages
+    WS_COL_STEPS = 8,   // steps of the column payload plan (-1: no plan)
     WS_ENC_TICKETS = 16,  // encode: ticket counters of the slice launches (one per part)
     WS_HDR_BYTES = 256
 };
@@ -149,9 +154,19 @@ enum {
 // The recipe of a pair is its padded row (f included and -1 padding, both
 // skipped by the payload), gathered in segments of kRecipeSeg entries. All
 // per-level ranges are 16-byte aligned so one bulk copy stages each.
+// The column payload plan (built after the path when the code fits that
+// kernel) is
+//   col_src[v]  = coded row whose payload starts intermediate v, or -1 (a
+//                 check, an unrecovered v, and v = k_int, the zero slot)
+//   col_seg[s]  = segment record: 8 uint16 {e0..e6, f}; e_i are the
+//                 intermediates at 7 consecutive positions of the row of g
+//                 (k_int where the entry is f or past the row's end)
+//   col_step[i] = first segment of step i; col_step[n_steps] = all segments.
+//                 A step is at most kColSegMax segments of one level.
 struct DecodeLayout {
     size_t res, xs, best, known, front_a, front_b, touched, pair_f, pair_g, pair_rec, level_off,
-        level_tab, seg_pair, chunk_pair, unrec_list, parity, total;
+        level_tab, seg_pair, chunk_pair, unrec_list, parity, col_src, col_step, col_seg, total;
+    int64_t col_max_segs, col_max_steps;
 };
 
 static inline DecodeLayout decode_layout(const fs_code *c) {
@@ -174,6 +189,13 @@ static inline DecodeLayout decode_layout(const fs_code *c) {
     L.chunk_pair = o; o = fs_align256(o + 4 * (4 * K + (size_t)c->e_con4 / 4 + 8));
     L.unrec_list = o; o = fs_align256(o + 4 * (K + 1));
     L.parity = o;     o = fs_align256(o + (size_t)c->m * (size_t)c->t);
+    // a constraint releases at most one intermediate, so the segments are at
+    // most sum over constraints of ceil(degree / 7) <= e_con / 7 + K
+    L.col_max_segs = (int64_t)c->e_con / kColSegEntries + (int64_t)K + 1;
+    L.col_max_steps = (int64_t)K + L.col_max_segs / kColSegMax + 2;
+    L.col_src = o;    o = fs_align256(o + 4 * (K + 1));
+    L.col_step = o;   o = fs_align256(o + 4 * ((size_t)L.col_max_steps + 1));
+    L.col_seg = o;    o = fs_align256(o + 16 * (size_t)L.col_max_segs);
     L.total = o;
     return L;
 }
@@ -266,6 +288,15 @@ cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws,
 // Payload of the decoding path.
 cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_t *ws,
                         cudaStream_t s);
+// Column payload (fs_peel_col.cu). col_fits: the code's intermediates fit one
+// CTA's shared memory as 16-byte slots (and 16-bit ids). The plan kernel runs
+// after the symbolic pass when the column payload is selected and col_fits
+// holds; the payload kernel then reads it (the symbolic pass marks the plan
+// absent, and the payload reports FS_ERR_INVALID without one).
+bool col_fits(const fs_code *c);
+cudaError_t launch_col_plan(const fs_code *c, uint8_t *ws, cudaStream_t s);
+cudaError_t launch_peel_col(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_t *ws,
+                            cudaStream_t s);
 
 // Update kernels.
 cudaError_t launch_update(const fs_code *c, const int32_t *idx, int32_t n_idx, const uint4 *d_new,

@@ -277,6 +277,7 @@ __device__ void finish_dpg(const DpgArgs &a, const LevelCursor &cur, const uint8
     if (threadIdx.x == 0) {
         *a.n_unrecovered = *s_cnt;
         a.hdr[WS_N_UNREC_DATA] = *s_cnt_data;
+        a.hdr[WS_COL_STEPS] = -1;  // no column payload plan for this path (yet)
     }
 }
 
@@ -984,8 +985,10 @@ DpgArgs dpg_args(const fs_code *c, const uint8_t *erased, uint8_t *ws, uint8_t *
 
 }  // namespace
 
-cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws, uint8_t *unrecovered,
-                       int32_t *n_unrecovered, cudaStream_t s) {
+namespace {
+
+cudaError_t launch_dpg_only(const fs_code *c, const uint8_t *erased, uint8_t *ws,
+                            uint8_t *unrecovered, int32_t *n_unrecovered, cudaStream_t s) {
     const DpgArgs a = dpg_args(c, erased, ws, unrecovered, n_unrecovered);
     const DpgCompactPlace cp = plan_dpg_compact(c);
     if (c->dpg_compact && cp.bytes >= 0) {
@@ -1005,6 +1008,17 @@ cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws, uin
     }
     k_dpg<<<1, kDpgThreads, (size_t)pl.bytes, s>>>(a, pl);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+// The symbolic pass, then, when the column payload is selected and the code
+// fits it, that payload's plan.
+cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws, uint8_t *unrecovered,
+                       int32_t *n_unrecovered, cudaStream_t s) {
+    cudaError_t e = launch_dpg_only(c, erased, ws, unrecovered, n_unrecovered, s);
+    if (e == cudaSuccess && c->peel_columns && col_fits(c)) e = launch_col_plan(c, ws, s);
+    return e;
 }
 
 namespace {
@@ -1046,6 +1060,7 @@ PeelArgs peel_args(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_
 
 cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_t *ws,
                         cudaStream_t s) {
+    if (c->peel_columns && col_fits(c)) return launch_peel_col(c, coded, data_out, ws, s);
     const PeelArgs a = peel_args(c, coded, data_out, ws);
     const int64_t Lw = a.L;
     const size_t smem = peel_smem_bytes(Lw);

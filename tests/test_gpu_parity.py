@@ -230,12 +230,18 @@ def test_zero_coded_rows():
     assert not _host(out).any() and _host(unrec).all() and int(_host(nun)[0]) == 4
 
 
-def _graph_from_rows(b, rows):
+def _csr(rows):
     ptr = np.zeros(len(rows) + 1, np.int32)
     for j, r in enumerate(rows):
         ptr[j + 1] = ptr[j] + len(r)
-    idx = np.array([v for r in rows for v in sorted(r)], dtype=np.int32)
-    return gen.Graph(b, 0, len(rows), np.zeros(1, np.int32), np.zeros(0, np.int32), ptr, idx)
+    return ptr, np.array([v for r in rows for v in sorted(r)], dtype=np.int32)
+
+
+def _graph_from_rows(b, rows, checks=()):
+    """LT rows over the intermediates and precode checks over the data."""
+    ptr, idx = _csr(rows)
+    pptr, pidx = _csr(list(checks))
+    return gen.Graph(b, len(checks), len(rows), pptr, pidx, ptr, idx)
 
 
 def _check_plain(g, t, erased, tuning=None):
@@ -248,7 +254,7 @@ def _check_plain(g, t, erased, tuning=None):
     _, cod = oracle.encode(g, data, t)
     cd = _dev(cod)
     out = torch.empty((g.b, t), dtype=torch.uint8, device="cuda")
-    unrec = torch.empty(g.b, dtype=torch.uint8, device="cuda")
+    unrec = torch.empty(g.b + g.m, dtype=torch.uint8, device="cuda")
     nun = torch.empty(1, dtype=torch.int32, device="cuda")
     ws = code.workspace(fs.OP_DECODE)
     code.decode(cd, _dev(erased), out, unrec, nun, ws)
@@ -259,36 +265,65 @@ def _check_plain(g, t, erased, tuning=None):
     view = code.decode_path(ws)
     assert view["n_levels"] == path.n_levels
     assert _path_levels(view) == path.levels()
+    if g.m:
+        _, par = oracle.peel(g, cod, path, t, with_parity=True)
+        got = _host(view["parity"]).reshape(g.m, t)
+        ok = path.unrecovered[g.b:] == 0
+        assert np.array_equal(got[ok], par[ok])
+    assert fs.Code.ws_status(ws) == fs.FS_OK
     return path
 
 
-def test_wide_level_takes_the_direct_path():
+@pytest.mark.parametrize("cols", [0, 1])
+def test_wide_level_takes_the_direct_path(cols):
     """600 degree-1 rows: one level of 600 pairs, more than a shared-memory
-    stage holds, so the payload reads the path straight from global memory."""
+    stage of the slice payload holds, so it reads the path straight from
+    global memory; the column payload has no segment for them."""
     b = 600
     rows = [[j] for j in range(b)] + [[j, (j + 1) % b] for j in range(40)]
     g = _graph_from_rows(b, rows)
     erased = np.zeros(len(rows), np.uint8)
     erased[gen.sample_indices(b, 30, 5)] = 1
-    path = _check_plain(g, 48, erased)
+    path = _check_plain(g, 48, erased, {_fs().TUNE_PEEL_COLUMNS: cols})
     assert max(len(s) for s in path.levels()) > 256
 
 
-def test_long_chain_takes_the_direct_path():
-    """Row 0 = {0}, row j = {j-1, j}: one symbol per level, 1100 levels."""
+@pytest.mark.parametrize("cols", [0, 1])
+def test_long_chain_takes_the_direct_path(cols):
+    """Row 0 = {0}, row j = {j-1, j}: one symbol per level, 1100 levels (the
+    column payload: 1099 steps of one segment)."""
     b = 1100
     rows = [[0]] + [[j - 1, j] for j in range(1, b)]
     g = _graph_from_rows(b, rows)
-    path = _check_plain(g, 32, np.zeros(b, np.uint8))
+    path = _check_plain(g, 32, np.zeros(b, np.uint8), {_fs().TUNE_PEEL_COLUMNS: cols})
     assert path.n_levels == b
 
 
+@pytest.mark.parametrize("cols", [0, 1])
+@pytest.mark.parametrize("t", [16, 4096 + 48])
+def test_wide_check_level_splits_into_steps(cols, t):
+    """64 precode checks of 32 data blocks each (check j: j, j + 64, ...);
+    every data block and parity has its own degree-1 row. Erasing rows 0..63
+    leaves each check one unknown, so one level recovers 64 data blocks from
+    zero-payload constraints of 33 members: 320 column segments, more than
+    one step of 256 holds."""
+    b, m = 2048, 64
+    checks = [[j + 64 * i for i in range(32)] for j in range(m)]
+    rows = [[v] for v in range(b + m)]
+    g = _graph_from_rows(b, rows, checks)
+    erased = np.zeros(len(rows), np.uint8)
+    erased[:64] = 1
+    path = _check_plain(g, t, erased, {_fs().TUNE_PEEL_COLUMNS: cols})
+    assert path.n_levels == 2 and not path.unrecovered.any()
+    assert all(gg >= len(rows) for f, gg in path.levels()[1])
+
+
 @pytest.mark.parametrize("knob,value", [(1, 2), (1, 4), (2, 1), (3, 0), (4, 1), (5, 0), (5, 2),
-                                        (5, 3)])
+                                        (5, 3), (7, 1)])
 def test_tuning_knobs_leave_results_unchanged(knob, value):
     """Payload CTAs per SM, one gather CTA per SM, general (not compact)
     decoding schedule, L2 eviction hints, row-gather encode, 16- and 32-byte
-    slice encode."""
+    slice encode, column payload."""
     import torch
     fs = _fs()
     case = Case(1500, 60, 2000, 4096 + 32, gen.DIST_FINITE40)
@@ -344,3 +379,29 @@ def test_large_code_encodes_in_parts(t):
     _, p, cd = pre.encode_gpu()
     par, cod = oracle.encode(pre.g, pre.data, pre.t)
     assert np.array_equal(_host(cd), cod) and np.array_equal(_host(p), par)
+
+
+def test_column_payload_without_its_plan_reports_invalid():
+    """The column payload's plan is built by the decoding schedule only when
+    that payload is selected; a payload run after a schedule without it
+    reports FS_ERR_INVALID in the workspace status and writes nothing."""
+    import torch
+    fs = _fs()
+    case = Case(300, 12, 400, 64, gen.DIST_FINITE40)
+    _, _, cd = case.encode_gpu()
+    er = _dev(_erased(case.n, 0.1, gen.SEED_ERASE))
+    out = torch.full((case.b, case.t), 0x5A, dtype=torch.uint8, device="cuda")
+    unrec = torch.empty(case.b + case.m, dtype=torch.uint8, device="cuda")
+    nun = torch.empty(1, dtype=torch.int32, device="cuda")
+    ws = case.code.workspace(fs.OP_DECODE)
+    case.code.decode_schedule(er, unrec, nun, ws)  # slice payload selected: no plan
+    case.code.set_tuning(fs.TUNE_PEEL_COLUMNS, 1)
+    case.code.decode_payload(cd, out, ws)
+    assert fs.Code.ws_status(ws) == fs.FS_ERR_INVALID
+    assert bool((out == 0x5A).all())
+    # with the plan (schedule run with the column payload selected) it decodes
+    ws2 = case.code.workspace(fs.OP_DECODE)
+    case.code.decode(cd, er, out, unrec, nun, ws2)
+    assert fs.Code.ws_status(ws2) == fs.FS_OK
+    want, _ = oracle.decode(case.g, _host(cd), _host(er), case.t)
+    assert np.array_equal(_host(out), want)
