@@ -35,6 +35,10 @@
  *                decoded symbols and constraints visited in a caller-given
  *                order; used only by tests to show the recovered set does
  *                not depend on the schedule.
+ *   or_cga     - Algorithm 4 (Check Generation Algorithm): check #2 and
+ *                check #3 equations from the LT generator matrix.
+ *   or_local_dpg / or_local_peel - repair of lost coded blocks by peeling
+ *                over check #3 groups, scheduled like Algorithm 5.
  *
  * Readings of the paper taken here (the paper is silent or ambiguous):
  *   - maxit of Algorithms 1 and 5 is unbounded: iterate until a level
@@ -47,6 +51,13 @@
  *     members and parity b+j with payload zero. Constraint index space:
  *     coded rows 0..n-1, then checks n..n+m-1.
  *   - Unrecovered data blocks are returned as zero bytes.
+ *   - Algorithm 4: zero_columns(B) counts the all-zero columns of B (the
+ *     loop's comment; the text says "nonzero"); k is the number of rows of
+ *     B, the k_int intermediates; an index listed twice in an LT row cancels.
+ *   - Repair from check #3 groups: the smallest offering group repairs a
+ *     block (the paper orders groups by cardinality so the smallest is used
+ *     first); ties go to the lowest group index; unrepaired lost blocks are
+ *     returned as zero bytes.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -258,4 +269,237 @@ int32_t or_peel_immediate(int32_t b, int32_t m, int32_t n,
         }
     }
     return recovered;
+}
+
+/* ---------------------------------------------------------------------------
+ * Local recovery groups (check #2 and check #3 equations) and repair from
+ * them.
+ *
+ * Sets of indices are sorted int32 arrays; the XOR of two GF(2) columns is
+ * the symmetric difference of their sets, and the weight w of a column is the
+ * size of its set.
+ */
+typedef struct {
+    int32_t *v;
+    int32_t len, cap;
+} or_set;
+
+static int set_reserve(or_set *s, int32_t cap)
+{
+    if (cap <= s->cap) return 0;
+    int32_t c = s->cap ? s->cap : 8;
+    while (c < cap) c *= 2;
+    int32_t *p = (int32_t *)realloc(s->v, (size_t)c * sizeof(int32_t));
+    if (!p) return -1;
+    s->v = p;
+    s->cap = c;
+    return 0;
+}
+
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* w(a XOR b): elements in exactly one of the two sets. */
+static int32_t set_xor_size(const or_set *a, const or_set *b)
+{
+    int32_t i = 0, j = 0, w = 0;
+    while (i < a->len && j < b->len) {
+        if (a->v[i] == b->v[j]) { i++; j++; }
+        else if (a->v[i] < b->v[j]) { i++; w++; }
+        else { j++; w++; }
+    }
+    return w + (a->len - i) + (b->len - j);
+}
+
+/* a = a XOR b, through tmp (which then holds the old a). */
+static int set_xor_into(or_set *a, const or_set *b, or_set *tmp)
+{
+    if (set_reserve(tmp, a->len + b->len + 1)) return -1;
+    int32_t i = 0, j = 0, w = 0;
+    while (i < a->len && j < b->len) {
+        if (a->v[i] == b->v[j]) { i++; j++; }
+        else if (a->v[i] < b->v[j]) tmp->v[w++] = a->v[i++];
+        else tmp->v[w++] = b->v[j++];
+    }
+    while (i < a->len) tmp->v[w++] = a->v[i++];
+    while (j < b->len) tmp->v[w++] = b->v[j++];
+    tmp->len = w;
+    or_set t = *a;
+    *a = *tmp;
+    *tmp = t;
+    return 0;
+}
+
+void or_free(void *p) { free(p); }
+
+/*
+ * Check Generation Algorithm (Algorithm 4, CGA; Section "Algorithm for
+ * Jointly Generating Check #2 and Check #3 Equations").
+ *
+ * B is the k x n generator matrix of the LT layer: column j is the set of
+ * intermediates of coded block j (row j of the lt CSR; an index listed twice
+ * cancels). L starts as the n x n identity (column j = {j}). A sweep takes
+ * j = 0..n-1 and, inside it, i = 0..n-1: when i != j, 2 w(b_j) > w(b_i) and
+ * w(b_j XOR b_i) < w(b_j), it sets b_j = b_j XOR b_i and l_j = l_j XOR l_i.
+ * Sweeps repeat while fewer than n - k columns of B are zero (the reading of
+ * zero_columns(B): the number of all-zero columns) and stop after a sweep
+ * that changed nothing, or after max_sweeps sweeps when max_sweeps > 0.
+ *
+ * Throughout, b_j is the XOR of the original columns named by l_j, so the
+ * coded blocks of l_j XOR to zero when b_j = 0 (a check #3 group) and to
+ * intermediate e when b_j = {e} (a check #2 equation).
+ *
+ * *out (malloc'ed; free with or_free) receives, for each column j in order,
+ * the record [w(b_j), e, |l_j|, l_j ...] with e the single member of b_j when
+ * w(b_j) == 1 and -1 otherwise; *out_len its length in ints. Returns the
+ * number of sweeps run, or -1 when memory runs out.
+ */
+int32_t or_cga(int32_t k, int32_t n, const int32_t *lt_ptr, const int32_t *lt_idx,
+               int32_t max_sweeps, int32_t **out, int64_t *out_len)
+{
+    *out = NULL;
+    *out_len = 0;
+    or_set *B = (or_set *)calloc((size_t)n + 1, sizeof(or_set));
+    or_set *L = (or_set *)calloc((size_t)n + 1, sizeof(or_set));
+    or_set tmp = {0}, row = {0};
+    int32_t sweeps = -1;
+    if (!B || !L) goto done;
+    for (int32_t j = 0; j < n; j++) {
+        int32_t d = lt_ptr[j + 1] - lt_ptr[j];
+        if (set_reserve(&row, d + 1) || set_reserve(&L[j], 1)) goto done;
+        memcpy(row.v, lt_idx + lt_ptr[j], (size_t)d * sizeof(int32_t));
+        qsort(row.v, (size_t)d, sizeof(int32_t), cmp_i32);
+        if (set_reserve(&B[j], d + 1)) goto done;
+        B[j].len = 0;
+        for (int32_t e = 0; e < d;) {  /* pairs of equal entries cancel */
+            int32_t c = 1;
+            while (e + c < d && row.v[e + c] == row.v[e]) c++;
+            if (c & 1) B[j].v[B[j].len++] = row.v[e];
+            e += c;
+        }
+        L[j].v[0] = j;
+        L[j].len = 1;
+    }
+    sweeps = 0;
+    for (;;) {
+        int32_t zero = 0;
+        for (int32_t j = 0; j < n; j++) zero += B[j].len == 0;
+        if (zero >= n - k) break;
+        if (max_sweeps > 0 && sweeps >= max_sweeps) break;
+        int changed = 0;
+        for (int32_t j = 0; j < n; j++) {
+            for (int32_t i = 0; i < n; i++) {
+                if (i == j || !(2 * B[j].len > B[i].len)) continue;
+                if (set_xor_size(&B[j], &B[i]) < B[j].len) {
+                    if (set_xor_into(&B[j], &B[i], &tmp) || set_xor_into(&L[j], &L[i], &tmp)) {
+                        sweeps = -1;
+                        goto done;
+                    }
+                    changed = 1;
+                }
+            }
+        }
+        sweeps++;
+        if (!changed) break;
+    }
+    int64_t len = 0;
+    for (int32_t j = 0; j < n; j++) len += 3 + L[j].len;
+    *out = (int32_t *)malloc((size_t)(len + 1) * sizeof(int32_t));
+    if (!*out) { sweeps = -1; goto done; }
+    int64_t o = 0;
+    for (int32_t j = 0; j < n; j++) {
+        (*out)[o++] = B[j].len;
+        (*out)[o++] = B[j].len == 1 ? B[j].v[0] : -1;
+        (*out)[o++] = L[j].len;
+        memcpy(*out + o, L[j].v, (size_t)L[j].len * sizeof(int32_t));
+        o += L[j].len;
+    }
+    *out_len = o;
+done:
+    if (B) for (int32_t j = 0; j < n; j++) free(B[j].v);
+    if (L) for (int32_t j = 0; j < n; j++) free(L[j].v);
+    free(B);
+    free(L);
+    free(tmp.v);
+    free(row.v);
+    return sweeps;
+}
+
+/*
+ * Repair of lost coded blocks from check #3 groups (the coded-only local
+ * groups; repair, like decoding, is BP, Section "Reading/Formating" and
+ * "Update Process"), scheduled like Algorithm 5: level by level, every group
+ * with exactly one lost and not yet repaired member f (counted against the
+ * state at the level start) offers f; each offered f takes the offering group
+ * of smallest cardinality, ties to the lowest group index; then every f of
+ * the level counts as repaired. It stops at a level with no offer.
+ * groups: G rows over coded block indices (0..n-1). Writes the pairs in level
+ * order (ascending f inside a level), their levels, the unrepaired flags (lost
+ * and not repaired), *n_levels; returns the number of pairs (-1: no memory).
+ */
+int32_t or_local_dpg(int32_t n, int32_t G, const int32_t *g_ptr, const int32_t *g_idx,
+                     const uint8_t *lost, int32_t *pair_f, int32_t *pair_g, int32_t *level_of,
+                     uint8_t *unrepaired, int32_t *n_levels)
+{
+    uint8_t *unknown = (uint8_t *)malloc((size_t)n + 1);
+    int32_t *best = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    if (!unknown || !best) { free(unknown); free(best); return -1; }
+    for (int32_t s = 0; s < n; s++) unknown[s] = lost[s] ? 1 : 0;
+    int32_t np = 0, level = 0;
+    for (;;) {
+        for (int32_t s = 0; s < n; s++) best[s] = -1;
+        for (int32_t g = 0; g < G; g++) {
+            int32_t cnt = 0, f = -1;
+            for (int32_t e = g_ptr[g]; e < g_ptr[g + 1]; e++)
+                if (unknown[g_idx[e]]) { cnt++; f = g_idx[e]; }
+            if (cnt != 1) continue;
+            int32_t card = g_ptr[g + 1] - g_ptr[g];
+            int32_t cur = best[f];
+            if (cur < 0 || card < g_ptr[cur + 1] - g_ptr[cur] ||
+                (card == g_ptr[cur + 1] - g_ptr[cur] && g < cur))
+                best[f] = g;
+        }
+        int32_t found = 0;
+        for (int32_t s = 0; s < n; s++) {
+            if (best[s] < 0) continue;
+            pair_f[np] = s;
+            pair_g[np] = best[s];
+            level_of[np] = level;
+            np++;
+            found++;
+        }
+        if (!found) break;
+        for (int32_t s = 0; s < n; s++)
+            if (best[s] >= 0) unknown[s] = 0;
+        level++;
+    }
+    for (int32_t s = 0; s < n; s++) unrepaired[s] = unknown[s];
+    *n_levels = level;
+    free(unknown);
+    free(best);
+    return np;
+}
+
+/*
+ * The payload of a repair path: for each pair (f, g) in order, coded block f
+ * becomes the XOR of the other members of group g (all known by then).
+ * coded is updated in place.
+ */
+int or_local_peel(int32_t n, const int32_t *g_ptr, const int32_t *g_idx, int64_t t,
+                  uint8_t *coded, int32_t npairs, const int32_t *pair_f, const int32_t *pair_g)
+{
+    (void)n;
+    for (int32_t p = 0; p < npairs; p++) {
+        int32_t f = pair_f[p], g = pair_g[p];
+        uint8_t *dst = coded + (int64_t)f * t;
+        memset(dst, 0, (size_t)t);
+        for (int32_t e = g_ptr[g]; e < g_ptr[g + 1]; e++) {
+            int32_t h = g_idx[e];
+            if (h != f) xor_into(dst, coded + (int64_t)h * t, t);
+        }
+    }
+    return 0;
 }
