@@ -222,6 +222,69 @@ typedef struct {
 fs_status fs_decode_path(const fs_code *code, const void *d_ws, fs_path_view *out);
 
 /*
+ * Local recovery groups and repair from them (Section "Generating
+ * Information for Efficient Repair", Algorithm 4 "Check Generation
+ * Algorithm", and the repair process that peels over the groups).
+ *
+ * fs_local_create builds, on the host, from the same graph arguments as
+ * fs_code_create:
+ *   1. Algorithm 4 on the LT generator matrix B (k_int rows, column j = the
+ *      intermediates of coded block j): sweeps over ordered column pairs
+ *      (j, i) replace b_j by b_j XOR b_i (and l_j by l_j XOR l_i, L starting
+ *      as the identity) when 2 w(b_j) > w(b_i) and w(b_j XOR b_i) < w(b_j),
+ *      until n - k_int columns of B are zero, a sweep changes nothing, or
+ *      max_sweeps sweeps ran (max_sweeps > 0). A zero column j gives the
+ *      check #3 group l_j (coded blocks that XOR to zero); a column reduced
+ *      to one intermediate i gives the check #2 equation x_i = XOR of l_j
+ *      (the first such column per i);
+ *   2. the set-XOR derivations: a coded block s of degree one over
+ *      intermediate i adds (check #2 set of i) XOR {s}; a precode check whose
+ *      members and parity all have check #2 sets adds the XOR of those sets;
+ *   3. empty and repeated groups dropped (the first kept), the groups ordered
+ *      by cardinality, ties in the order of steps 1-2.
+ * The host work is sweeps x n^2 sorted-set comparisons (seconds at n ~ 5000).
+ * Unless flags has FS_LOCAL_HOST_ONLY, the check #3 groups and their
+ * transpose are copied to the current device. *out is set only on FS_OK.
+ */
+typedef struct fs_local fs_local; /* opaque; owned by the library */
+#define FS_LOCAL_HOST_ONLY 1
+fs_status fs_local_create(const fs_csr *precode, const fs_csr *lt, int32_t max_sweeps, int flags,
+                          fs_local **out);
+void fs_local_destroy(fs_local *local);
+/* Sizes (any out pointer may be NULL): coded blocks, intermediates, check #3
+ * groups and their total entries, check #2 equations and their total entries,
+ * Algorithm 4 sweeps run. */
+fs_status fs_local_info(const fs_local *local, int32_t *n, int32_t *k_int, int32_t *n_groups,
+                        int64_t *group_entries, int32_t *n_check2, int64_t *check2_entries,
+                        int32_t *sweeps);
+/* Host copies. Check #3 groups in repair order as CSR: ptr[n_groups + 1],
+ * idx[group_entries] (ascending coded indices per group). Check #2
+ * equations in intermediate order: inter[n_check2], ptr[n_check2 + 1],
+ * idx[check2_entries]. */
+fs_status fs_local_groups(const fs_local *local, int32_t *ptr, int32_t *idx);
+fs_status fs_local_check2(const fs_local *local, int32_t *inter, int32_t *ptr, int32_t *idx);
+/* Device workspace of fs_repair_local (caller-owned, 16-byte aligned). */
+size_t fs_local_workspace_bytes(const fs_local *local);
+/*
+ * Repairs lost coded blocks in place from the check #3 groups: d_lost[n]
+ * flags (nonzero = lost), d_coded the n stored blocks of block_bytes each
+ * (a multiple of 16; the lost ones are overwritten). Level by level, every
+ * group with exactly one lost, not yet repaired member offers it; each
+ * offered block takes the smallest offering group (ties: lowest group
+ * index) and becomes the XOR of that group's other members; then the level's
+ * blocks count as repaired. Lost blocks left unrepaired are zeroed and
+ * flagged in d_unrepaired[n]; *d_n_unrepaired counts them. Asynchronous on
+ * stream; FS_ERR_INVALID for a host-only fs_local or bad arguments.
+ */
+fs_status fs_repair_local(const fs_local *local, const uint8_t *d_lost, void *d_coded,
+                          size_t block_bytes, uint8_t *d_unrepaired, int32_t *d_n_unrepaired,
+                          void *d_ws, void *stream);
+/* The repair path of the last fs_repair_local on d_ws, as device views: pair
+ * (f, g) = coded block f from group g, levels as in fs_decode_path; parity is
+ * NULL. */
+fs_status fs_local_path(const fs_local *local, const void *d_ws, fs_path_view *out);
+
+/*
  * Update: data blocks d_idx[q] (q < n_idx, distinct, each < b) are replaced
  * by d_new[q*t .. (q+1)*t). For each one, delta = old XOR new is XORed into
  * every parity whose check contains it and every coded block whose

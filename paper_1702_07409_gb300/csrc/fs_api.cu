@@ -10,8 +10,6 @@
 #include "fs_internal.cuh"
 
 
-namespace {
-
 bool csr_ok(const fs_csr *g, int32_t n_rows_expect, int32_t n_cols_expect) {
     if (!g) return false;
     if (g->n_rows < 0 || g->n_cols < 0) return false;
@@ -31,6 +29,8 @@ bool csr_ok(const fs_csr *g, int32_t n_rows_expect, int32_t n_cols_expect) {
     }
     return true;
 }
+
+namespace {
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 

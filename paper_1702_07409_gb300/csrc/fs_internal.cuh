@@ -73,6 +73,10 @@ struct fs_code {
     SlicePart sl_part[kSliceParts];
 };
 
+// A CSR with rows of strictly ascending in-range column indices (and the
+// expected shape where an expectation is >= 0).
+bool csr_ok(const fs_csr *g, int32_t n_rows_expect, int32_t n_cols_expect);
+
 // Builds the slice encode tables of c (host arrays of the joint graph);
 // leaves sl_slots = 0 when the code does not fit.
 cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t *con_idx);

@@ -31,7 +31,10 @@ EXPORTS = ("fs_code_create", "fs_code_destroy", "fs_code_info", "fs_code_set_tun
            "fs_encode", "fs_encode_static", "fs_encode_rows", "fs_decode", "fs_decode_schedule",
            "fs_decode_payload", "fs_decode_path", "fs_update", "fs_repair",
            "fs_batch_create", "fs_batch_run", "fs_batch_status", "fs_batch_destroy",
-           "fs_selftest_timeout", "fs_status_string")
+           "fs_selftest_timeout", "fs_status_string",
+           "fs_local_create", "fs_local_destroy", "fs_local_info", "fs_local_groups",
+           "fs_local_check2", "fs_local_workspace_bytes", "fs_repair_local", "fs_local_path")
+LOCAL_HOST_ONLY = 1
 
 
 class _Stripe(ctypes.Structure):
@@ -107,6 +110,22 @@ def lib() -> ctypes.CDLL:
         L.fs_batch_destroy.restype = None
         L.fs_selftest_timeout.argtypes = [vp, vp]
         L.fs_selftest_timeout.restype = ctypes.c_int
+        L.fs_local_create.argtypes = [vp, vp, i32, ctypes.c_int, ctypes.POINTER(vp)]
+        L.fs_local_create.restype = ctypes.c_int
+        L.fs_local_destroy.argtypes = [vp]
+        L.fs_local_destroy.restype = None
+        L.fs_local_info.argtypes = [vp] + [vp] * 7
+        L.fs_local_info.restype = ctypes.c_int
+        L.fs_local_groups.argtypes = [vp, vp, vp]
+        L.fs_local_groups.restype = ctypes.c_int
+        L.fs_local_check2.argtypes = [vp, vp, vp, vp]
+        L.fs_local_check2.restype = ctypes.c_int
+        L.fs_local_workspace_bytes.argtypes = [vp]
+        L.fs_local_workspace_bytes.restype = sz
+        L.fs_repair_local.argtypes = [vp, vp, vp, sz, vp, vp, vp, vp]
+        L.fs_repair_local.restype = ctypes.c_int
+        L.fs_local_path.argtypes = [vp, vp, ctypes.POINTER(_PathView)]
+        L.fs_local_path.restype = ctypes.c_int
         L.fs_status_string.argtypes = [ctypes.c_int]
         L.fs_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -353,3 +372,108 @@ def selftest_timeout(stream=None) -> int:
     st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
     _check(lib().fs_selftest_timeout(_addr(st), _stream(stream)), "fs_selftest_timeout")
     return int(st.item())
+
+
+class Local:
+    """Local recovery groups of a graph and repair from them
+    (fs_local_create / fs_repair_local): check #2 equations and check #3
+    groups by Algorithm 4 and the set-XOR derivations, built on the host; the
+    repair peels over the check #3 groups on the device. ``host_only`` skips
+    the device copy (groups only, no repair)."""
+
+    def __init__(self, graph, max_sweeps: int = 0, host_only: bool = False):
+        if not host_only:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device: the Founsure GPU library has no CPU path")
+        self.b, self.m, self.n = int(graph.b), int(graph.m), int(graph.n)
+        self.k_int = self.b + self.m
+        self._keep = []
+        pre = None
+        if self.m > 0:
+            pp = np.ascontiguousarray(graph.pre_ptr, np.int32)
+            pi = np.ascontiguousarray(graph.pre_idx, np.int32)
+            self._keep += [pp, pi]
+            pre = _Csr(self.m, self.b, pp.ctypes.data, pi.ctypes.data if pi.size else None)
+        lp = np.ascontiguousarray(graph.lt_ptr, np.int32)
+        li = np.ascontiguousarray(graph.lt_idx, np.int32)
+        self._keep += [lp, li]
+        lt = _Csr(self.n, self.k_int, lp.ctypes.data, li.ctypes.data if li.size else None)
+        h = ctypes.c_void_p()
+        self._lib = lib()
+        rc = self._lib.fs_local_create(ctypes.byref(pre) if pre is not None else None,
+                                       ctypes.byref(lt), int(max_sweeps),
+                                       LOCAL_HOST_ONLY if host_only else 0, ctypes.byref(h))
+        _check(rc, "fs_local_create")
+        self._h = h
+
+    def info(self) -> dict:
+        n, k, g, c2 = (ctypes.c_int32() for _ in range(4))
+        ge, c2e = ctypes.c_int64(), ctypes.c_int64()
+        sw = ctypes.c_int32()
+        _check(self._lib.fs_local_info(self._h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(g),
+                                       ctypes.byref(ge), ctypes.byref(c2), ctypes.byref(c2e),
+                                       ctypes.byref(sw)), "fs_local_info")
+        return dict(n=n.value, k_int=k.value, n_groups=g.value, group_entries=ge.value,
+                    n_check2=c2.value, check2_entries=c2e.value, sweeps=sw.value)
+
+    def groups(self):
+        """Check #3 groups in repair order: (ptr, idx) int32 arrays."""
+        i = self.info()
+        ptr = np.zeros(i["n_groups"] + 1, np.int32)
+        idx = np.zeros(max(i["group_entries"], 1), np.int32)
+        _check(self._lib.fs_local_groups(self._h, ptr.ctypes.data, idx.ctypes.data),
+               "fs_local_groups")
+        return ptr, idx[:i["group_entries"]]
+
+    def check2(self) -> dict:
+        """Check #2 equations: {intermediate: tuple of coded blocks}."""
+        i = self.info()
+        inter = np.zeros(max(i["n_check2"], 1), np.int32)
+        ptr = np.zeros(i["n_check2"] + 1, np.int32)
+        idx = np.zeros(max(i["check2_entries"], 1), np.int32)
+        _check(self._lib.fs_local_check2(self._h, inter.ctypes.data, ptr.ctypes.data,
+                                         idx.ctypes.data), "fs_local_check2")
+        return {int(inter[q]): tuple(int(x) for x in idx[ptr[q]:ptr[q + 1]])
+                for q in range(i["n_check2"])}
+
+    def workspace(self, device=None):
+        import torch
+        return torch.empty(max(int(self._lib.fs_local_workspace_bytes(self._h)), 256),
+                           dtype=torch.uint8, device=device or "cuda")
+
+    def repair(self, lost, coded, block_bytes: int, unrepaired, n_unrepaired, ws,
+               stream=None) -> None:
+        """Repairs the lost coded blocks of ``coded`` in place (fs_repair_local)."""
+        _check(self._lib.fs_repair_local(self._h, _addr(lost), _addr(coded), int(block_bytes),
+                                         _addr(unrepaired), _addr(n_unrepaired), _addr(ws),
+                                         _stream(stream)), "fs_repair_local")
+
+    def path(self, ws):
+        """Levels of the last repair on ws (synchronises): list of sets {(f, g)}."""
+        import torch
+        v = _PathView()
+        _check(self._lib.fs_local_path(self._h, _addr(ws), ctypes.byref(v)), "fs_local_path")
+        base = ws.data_ptr()
+
+        def at(ptr, count):
+            off = ptr - base
+            return ws[off:off + 4 * count].view(torch.int32).cpu().numpy()
+
+        torch.cuda.synchronize()
+        nl = int(at(v.n_levels, 1)[0])
+        npairs = int(at(v.n_pairs, 1)[0])
+        lo, f, g = at(v.level_off, nl + 1), at(v.pair_f, npairs), at(v.pair_g, npairs)
+        return [set(zip(f[lo[l]:lo[l + 1]].tolist(), g[lo[l]:lo[l + 1]].tolist()))
+                for l in range(nl)]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.fs_local_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
