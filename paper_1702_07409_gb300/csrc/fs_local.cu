@@ -19,10 +19,15 @@
 //     repaired and xs = the XOR of their indices, so a group with res == 1
 //     names its unknown without a scan; each offered block takes the offering
 //     group with the lowest (cardinality, index) key by a 64-bit atomicMin.
+//     It then cuts every pair's group into chunks of kLocalChunk members (a
+//     block scan gives each pair its first chunk) so that long groups spread
+//     over many threads.
 //   k_local_peel: each CTA owns a slice of 16-byte words of every block and
 //     walks all levels (pairs of a level are independent: a level only reads
-//     blocks repaired in earlier levels), one thread per (pair, word), a
-//     __syncthreads between levels; repaired blocks are written in place.
+//     blocks repaired in earlier levels). One thread per (chunk, word) XORs
+//     the chunk's members (eight loads in flight) and folds the result into a
+//     shared-memory accumulator of its (pair, word) with 32-bit shared XOR
+//     reductions; after a barrier the accumulators are written in place.
 #include <stdlib.h>
 #include <string.h>
 
@@ -191,32 +196,79 @@ void free_local(fs_local *o) {
 }
 
 // ---- workspace ---------------------------------------------------------------
-enum { LW_STATUS = 0, LW_N_LEVELS = 1, LW_N_PAIRS = 2, LW_N_UNREP = 3 };
+enum { LW_STATUS = 0, LW_N_LEVELS = 1, LW_N_PAIRS = 2, LW_N_UNREP = 3, LW_N_CHUNKS = 4 };
+
+constexpr int kLocalDpgThreads = 1024;
+constexpr int kLocalPeelThreads = 256;
+constexpr int kLocalPeelCtasPerSm = 4;
+constexpr int kLocalChunk = 64;     // group members one payload thread XORs
+constexpr int kLocalAcc = 2048;     // (pair, word) accumulators of one payload CTA
 
 struct LocalLayout {
-    size_t res, xs, best, unknown, pair_f, pair_g, level_off, unrep, total;
+    size_t res, xs, best, unknown, pair_f, pair_g, level_off, unrep, choff, chunk_pair,
+        chunk_e0, level_chunk, total;
 };
 
 LocalLayout local_layout(const fs_local *o) {
     LocalLayout L;
     const size_t G = o->g_ptr.size() - 1, n = (size_t)o->n;
+    // a group repairs at most one block, so the chunks are at most
+    // sum over groups of ceil(|g| / kLocalChunk) <= entries / kLocalChunk + groups
+    const size_t chunks = o->g_idx.size() / kLocalChunk + G + 1;
     size_t p = WS_HDR_BYTES;
-    L.res = p;       p = fs_align256(p + 4 * (G + 1));
-    L.xs = p;        p = fs_align256(p + 4 * (G + 1));
-    L.best = p;      p = fs_align256(p + 8 * (n + 1));
-    L.unknown = p;   p = fs_align256(p + (n + 1));
-    L.pair_f = p;    p = fs_align256(p + 4 * (n + 1));
-    L.pair_g = p;    p = fs_align256(p + 4 * (n + 1));
-    L.level_off = p; p = fs_align256(p + 4 * (n + 2));
-    L.unrep = p;     p = fs_align256(p + 4 * (n + 1));
+    L.res = p;         p = fs_align256(p + 4 * (G + 1));
+    L.xs = p;          p = fs_align256(p + 4 * (G + 1));
+    L.best = p;        p = fs_align256(p + 8 * (n + 1));
+    L.unknown = p;     p = fs_align256(p + (n + 1));
+    L.pair_f = p;      p = fs_align256(p + 4 * (n + 1));
+    L.pair_g = p;      p = fs_align256(p + 4 * (n + 1));
+    L.level_off = p;   p = fs_align256(p + 4 * (n + 2));
+    L.unrep = p;       p = fs_align256(p + 4 * (n + 1));
+    L.choff = p;       p = fs_align256(p + 4 * (n + 1));
+    L.chunk_pair = p;  p = fs_align256(p + 4 * chunks);
+    L.chunk_e0 = p;    p = fs_align256(p + 4 * chunks);
+    L.level_chunk = p; p = fs_align256(p + 4 * (n + 2));
     L.total = p;
     return L;
 }
 
 // ---- kernels -----------------------------------------------------------------
-constexpr int kLocalDpgThreads = 1024;
-constexpr int kLocalPeelThreads = 256;
-constexpr int kLocalPeelCtasPerSm = 4;
+
+// In-place exclusive prefix sum of v[0, n) (global memory, read and written by
+// the calling block only); returns the total to every thread. s_warp holds 33
+// ints.
+__device__ int32_t block_scan_global(int32_t *v, int32_t n, int32_t *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int32_t carry = 0;
+    for (int32_t base = 0; base < n; base += blockDim.x) {
+        const int32_t i = base + threadIdx.x;
+        const int32_t x = i < n ? v[i] : 0;
+        int32_t inc = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += y;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const int32_t t = lane < nw ? s_warp[lane] : 0;
+            int32_t ti = t;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, ti, d);
+                if (lane >= d) ti += y;
+            }
+            s_warp[lane] = ti - t;
+            if (lane == 31) s_warp[32] = ti;
+        }
+        __syncthreads();
+        if (i < n) v[i] = carry + s_warp[warp] + inc - x;
+        carry += s_warp[32];
+        __syncthreads();
+    }
+    return carry;
+}
 
 struct LocalDpgArgs {
     const int32_t *gptr, *gidx, *tptr, *tidx;
@@ -224,6 +276,7 @@ struct LocalDpgArgs {
     int32_t n, G;
     int32_t *hdr;
     int32_t *res, *xs, *pair_f, *pair_g, *level_off, *unrep;
+    int32_t *choff, *chunk_pair, *chunk_e0, *level_chunk;
     unsigned long long *best;
     uint8_t *unknown, *unrepaired;
     int32_t *n_unrepaired;
@@ -231,6 +284,7 @@ struct LocalDpgArgs {
 
 __global__ void __launch_bounds__(kLocalDpgThreads) k_local_dpg(LocalDpgArgs a) {
     __shared__ int32_t s_np, s_cnt, s_level, s_nu;
+    __shared__ int32_t s_warp[33];
     for (int32_t g = threadIdx.x; g < a.G; g += blockDim.x) {
         a.res[g] = 0;
         a.xs[g] = 0;
@@ -301,12 +355,32 @@ __global__ void __launch_bounds__(kLocalDpgThreads) k_local_dpg(LocalDpgArgs a) 
         a.unrepaired[s] = u;
         if (u) a.unrep[atomicAdd(&s_nu, 1)] = s;
     }
+    // chunks of every pair's group, in pair order; level l owns chunks
+    // [level_chunk[l], level_chunk[l + 1])
+    const int32_t np = s_np, nl = s_level;
+    for (int32_t p = threadIdx.x; p < np; p += blockDim.x) {
+        const int32_t g = a.pair_g[p];
+        a.choff[p] = (a.gptr[g + 1] - a.gptr[g] + kLocalChunk - 1) / kLocalChunk;
+    }
     __syncthreads();
+    const int32_t n_chunks = block_scan_global(a.choff, np, s_warp);
+    if (threadIdx.x == 0) a.choff[np] = n_chunks;
+    __syncthreads();
+    for (int32_t p = threadIdx.x; p < np; p += blockDim.x) {
+        const int32_t g = a.pair_g[p], c0 = a.choff[p], nch = a.choff[p + 1] - c0;
+        for (int32_t c = 0; c < nch; ++c) {
+            a.chunk_pair[c0 + c] = p;
+            a.chunk_e0[c0 + c] = a.gptr[g] + c * kLocalChunk;
+        }
+    }
+    if (threadIdx.x == 0) a.level_off[nl] = np;
+    __syncthreads();
+    for (int32_t l = threadIdx.x; l <= nl; l += blockDim.x) a.level_chunk[l] = a.choff[a.level_off[l]];
     if (threadIdx.x == 0) {
-        a.level_off[s_level] = s_np;
-        a.hdr[LW_N_LEVELS] = s_level;
-        a.hdr[LW_N_PAIRS] = s_np;
+        a.hdr[LW_N_LEVELS] = nl;
+        a.hdr[LW_N_PAIRS] = np;
         a.hdr[LW_N_UNREP] = s_nu;
+        a.hdr[LW_N_CHUNKS] = n_chunks;
         *a.n_unrepaired = s_nu;
     }
 }
@@ -314,53 +388,75 @@ __global__ void __launch_bounds__(kLocalDpgThreads) k_local_dpg(LocalDpgArgs a) 
 struct LocalPeelArgs {
     uint4 *coded;
     const int32_t *gptr, *gidx, *pair_f, *pair_g, *level_off, *unrep, *hdr;
+    const int32_t *choff, *chunk_pair, *chunk_e0, *level_chunk;
     int64_t tw;
     int32_t L;  // words of every block per CTA
 };
 
-__global__ void __launch_bounds__(kLocalPeelThreads, kLocalPeelCtasPerSm) k_local_peel(LocalPeelArgs a) {
+__device__ __forceinline__ void red_xor16(uint4 *d, const uint4 &v) {
+    const uint32_t p = (uint32_t)__cvta_generic_to_shared(d);
+    asm volatile("red.shared.xor.b32 [%0], %1;\n" ::"r"(p), "r"(v.x) : "memory");
+    asm volatile("red.shared.xor.b32 [%0], %1;\n" ::"r"(p + 4), "r"(v.y) : "memory");
+    asm volatile("red.shared.xor.b32 [%0], %1;\n" ::"r"(p + 8), "r"(v.z) : "memory");
+    asm volatile("red.shared.xor.b32 [%0], %1;\n" ::"r"(p + 12), "r"(v.w) : "memory");
+}
+
+__global__ void __launch_bounds__(kLocalPeelThreads, kLocalPeelCtasPerSm)
+    k_local_peel(LocalPeelArgs a) {
+    __shared__ uint4 s_acc[kLocalAcc];
     const int64_t w0 = (int64_t)blockIdx.x * a.L;
     const int32_t lanes = (int32_t)min((int64_t)a.L, a.tw - w0);
     if (lanes <= 0) return;
+    for (int32_t i = threadIdx.x; i < kLocalAcc; i += blockDim.x) s_acc[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
     const int32_t nl = a.hdr[LW_N_LEVELS];
+    const int32_t per = kLocalAcc / lanes;  // pairs whose accumulators fit at once
     for (int32_t l = 0; l < nl; ++l) {
-        const int32_t p0 = a.level_off[l], p1 = a.level_off[l + 1];
-        const int32_t items = (p1 - p0) * lanes;
-        for (int32_t it = threadIdx.x; it < items; it += blockDim.x) {
-            const int32_t q = it / lanes, lane = it - q * lanes;
-            const int32_t f = a.pair_f[p0 + q], g = a.pair_g[p0 + q];
-            const int64_t w = w0 + lane;
-            uint4 acc = make_uint4(0, 0, 0, 0);
-            int32_t e = a.gptr[g];
-            const int32_t e1 = a.gptr[g + 1];
-            for (; e + 4 <= e1; e += 4) {  // four loads in flight
-                uint4 v[4];
-                int32_t h[4];
+        const int32_t p1 = a.level_off[l + 1];
+        for (int32_t pb = a.level_off[l]; pb < p1; pb += per) {
+            const int32_t pe = min(p1, pb + per);
+            const int32_t cb = a.choff[pb], items = (a.choff[pe] - cb) * lanes;
+            for (int32_t it = threadIdx.x; it < items; it += blockDim.x) {
+                const int32_t ci = cb + it / lanes, lane = it % lanes;
+                const int32_t p = a.chunk_pair[ci], f = a.pair_f[p], g = a.pair_g[p];
+                const int32_t e0 = a.chunk_e0[ci], e1 = min(e0 + kLocalChunk, a.gptr[g + 1]);
+                const int64_t w = w0 + lane;
+                uint4 acc = make_uint4(0, 0, 0, 0);
+                int32_t e = e0;
+                for (; e + 8 <= e1; e += 8) {  // eight loads in flight
+                    uint4 v[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    h[u] = __ldg(a.gidx + e + u);
-                    v[u] = h[u] != f ? a.coded[(int64_t)h[u] * a.tw + w] : make_uint4(0, 0, 0, 0);
-                }
+                    for (int u = 0; u < 8; ++u) {
+                        const int32_t h = __ldg(a.gidx + e + u);
+                        v[u] = h != f ? a.coded[(int64_t)h * a.tw + w] : make_uint4(0, 0, 0, 0);
+                    }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    acc.x ^= v[u].x;
-                    acc.y ^= v[u].y;
-                    acc.z ^= v[u].z;
-                    acc.w ^= v[u].w;
+                    for (int u = 0; u < 8; ++u) {
+                        acc.x ^= v[u].x;
+                        acc.y ^= v[u].y;
+                        acc.z ^= v[u].z;
+                        acc.w ^= v[u].w;
+                    }
                 }
+                for (; e < e1; ++e) {
+                    const int32_t h = __ldg(a.gidx + e);
+                    if (h == f) continue;
+                    const uint4 v = a.coded[(int64_t)h * a.tw + w];
+                    acc.x ^= v.x;
+                    acc.y ^= v.y;
+                    acc.z ^= v.z;
+                    acc.w ^= v.w;
+                }
+                red_xor16(s_acc + (p - pb) * lanes + lane, acc);
             }
-            for (; e < e1; ++e) {
-                const int32_t h = __ldg(a.gidx + e);
-                if (h == f) continue;
-                const uint4 v = a.coded[(int64_t)h * a.tw + w];
-                acc.x ^= v.x;
-                acc.y ^= v.y;
-                acc.z ^= v.z;
-                acc.w ^= v.w;
+            __syncthreads();
+            for (int32_t it = threadIdx.x; it < (pe - pb) * lanes; it += blockDim.x) {
+                const int32_t q = it / lanes, lane = it - q * lanes;
+                a.coded[(int64_t)a.pair_f[pb + q] * a.tw + w0 + lane] = s_acc[it];
+                s_acc[it] = make_uint4(0, 0, 0, 0);
             }
-            a.coded[(int64_t)f * a.tw + w] = acc;
+            __syncthreads();
         }
-        __syncthreads();
     }
     const int32_t nu = a.hdr[LW_N_UNREP];
     for (int32_t it = threadIdx.x; it < nu * lanes; it += blockDim.x) {
@@ -490,6 +586,10 @@ FS_API fs_status fs_repair_local(const fs_local *o, const uint8_t *d_lost, void 
     a.pair_g = reinterpret_cast<int32_t *>(w + L.pair_g);
     a.level_off = reinterpret_cast<int32_t *>(w + L.level_off);
     a.unrep = reinterpret_cast<int32_t *>(w + L.unrep);
+    a.choff = reinterpret_cast<int32_t *>(w + L.choff);
+    a.chunk_pair = reinterpret_cast<int32_t *>(w + L.chunk_pair);
+    a.chunk_e0 = reinterpret_cast<int32_t *>(w + L.chunk_e0);
+    a.level_chunk = reinterpret_cast<int32_t *>(w + L.level_chunk);
     a.unrepaired = d_unrepaired;
     a.n_unrepaired = d_n_unrepaired;
     k_local_dpg<<<1, kLocalDpgThreads, 0, s>>>(a);
@@ -504,11 +604,17 @@ FS_API fs_status fs_repair_local(const fs_local *o, const uint8_t *d_lost, void 
     p.level_off = a.level_off;
     p.unrep = a.unrep;
     p.hdr = a.hdr;
+    p.choff = a.choff;
+    p.chunk_pair = a.chunk_pair;
+    p.chunk_e0 = a.chunk_e0;
+    p.level_chunk = a.level_chunk;
     p.tw = (int64_t)(block_bytes / 16);
     int64_t ctas = (int64_t)o->num_sms * kLocalPeelCtasPerSm;
     if (ctas > p.tw) ctas = p.tw;
-    p.L = (int32_t)((p.tw + ctas - 1) / ctas);
-    ctas = (p.tw + p.L - 1) / p.L;
+    int64_t Lw = (p.tw + ctas - 1) / ctas;
+    if (Lw > kLocalAcc) Lw = kLocalAcc;  // a pair's accumulators fit beside the others
+    p.L = (int32_t)Lw;
+    ctas = (p.tw + Lw - 1) / Lw;
     k_local_peel<<<(unsigned)ctas, kLocalPeelThreads, 0, s>>>(p);
     return cudaGetLastError() == cudaSuccess ? FS_OK : FS_ERR_CUDA;
 }
