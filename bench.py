@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -743,6 +744,89 @@ def run_repair_local(args):
         print(json.dumps(line), flush=True)
 
 
+def run_simdisk(args):
+    """The paper's simDisk sweep at the precoded stripe (b = 4096, m = 128,
+    n = 5400): the coded blocks striped over 10 disks (540 each), every
+    combination of 1-4 failed disks (10 + 45 + 120 + 210 = 385 erasure
+    patterns), each a symbolic decode (Algorithm 5, no payload). One step =
+    one batch of all patterns (fs_batch, FS_OP_SCHEDULE; one CTA per pattern),
+    device-timed; the patterns' outcomes are checked against the oracle on a
+    sample. cpu_baseline: the oracle's schedule on a sample of the patterns."""
+    import torch
+    from paper_1702_07409_gb300 import founsure as fs
+    from paper_1702_07409_gb300 import simdisk
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    disks, fmax = 10, 4
+    g = gen.make_graph(B, M, N_CODED, gen.DIST_FINITE40)
+    sd = simdisk.SimDisk(g, disks, device=device)
+    code, n, k = sd.code, N_CODED, B + M
+    combos, flags = [], []
+    for f in range(1, fmax + 1):
+        c, fl = simdisk.failure_patterns(n, disks, f)
+        combos += c
+        flags.append(fl)
+    flags = np.concatenate(flags)
+    P = flags.shape[0]
+    d_er = torch.from_numpy(flags).to(device)
+    unrec = torch.empty((P, k), dtype=torch.uint8, device=device)
+    nun = torch.empty(P, dtype=torch.int32, device=device)
+    ws = torch.empty((P, sd.ws_bytes), dtype=torch.uint8, device=device)
+    stripes = [{"code": code, "erased": d_er.data_ptr() + i * n,
+                "unrecovered": unrec.data_ptr() + i * k, "n_unrecovered": nun.data_ptr() + 4 * i,
+                "ws": ws.data_ptr() + i * sd.ws_bytes} for i in range(P)]
+    batch = fs.Batch(stripes, fs.OP_SCHEDULE)
+    for _ in range(args.warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    K = args.steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record()
+        for _ in range(K):
+            batch.run()
+        e1.record()
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    ms = e0.elapsed_time(e1) / K
+    got = nun.cpu().numpy()
+    # cpu_baseline leg: the oracle's schedule on a sample of the patterns (its
+    # outcomes must also equal the batch's)
+    import oracle
+    oracle.build()
+    sample = list(range(0, P, max(1, P // 12)))[:12]
+    t0 = time.perf_counter()
+    for i in sample:
+        if int(oracle.dpg(g, flags[i]).unrecovered.sum()) != int(got[i]):
+            raise RuntimeError("simDisk pattern %d differs from the oracle" % i)
+    cpu_s = (time.perf_counter() - t0) / len(sample)
+    per_f, o = {}, 0
+    for f in range(1, fmax + 1):
+        c = math.comb(disks, f)
+        per_f[str(f)] = {"patterns": c, "tolerated": round(float(np.mean(got[o:o + c] == 0)), 4)}
+        o += c
+    line = {
+        "metric": "simDisk erasure patterns per second", "value": round(P / (ms * 1e-3), 1),
+        "unit": "patterns/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
+        "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (splitmix64 graph)",
+        "config": {"workload": "precoded stripe b=4096, m=128, n=5400 striped over %d disks "
+                               "(%d blocks each); every combination of 1-%d failed disks, one "
+                               "symbolic decode each" % (disks, -(-n // disks), fmax),
+                   "patterns": P},
+        "by_failures": per_f,
+        "cpu_baseline": {"value": round(1.0 / cpu_s, 2), "unit": "patterns/s", "cores": 1,
+                         "kind": "oracle", "sample": "%d of the %d patterns" % (len(sample), P)},
+        "gpu_launches": 1 * K,
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                   "reasons": clocks["reasons"]},
+    }
+    batch.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_serving(args):
     """Requests served from device-resident stripes (paper_1702_07409_gb300.serve):
     Poisson arrivals (mean 2000 requests/s, seeded exponential gaps) of encode
@@ -866,11 +950,12 @@ def main():
     ap.add_argument("--gather-ctas", type=int, default=0, help="tuning knob (1..16)")
 
     ap.add_argument("--workload", default="stripe",
-                    choices=["stripe", "batched", "serving", "repair_local"],
+                    choices=["stripe", "batched", "serving", "repair_local", "simdisk"],
                     help="stripe: the precoded stripe step (default); batched: many uneven "
                          "stripes through fs_batch vs per-stripe calls; serving: a Poisson "
                          "stream of requests on resident stripes; repair_local: repair of 5%% "
-                         "lost coded blocks from local recovery groups")
+                         "lost coded blocks from local recovery groups; simdisk: every "
+                         "combination of 1-4 failed disks out of 10, symbolic decodes")
     ap.add_argument("--requests", type=int, default=2000, help="requests of --workload serving")
     ap.add_argument("--rate", type=float, default=2000.0, help="mean arrivals per second (serving)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="HBM budget (serving)")
@@ -889,6 +974,8 @@ def main():
         run_serving(args)
     elif args.workload == "repair_local":
         run_repair_local(args)
+    elif args.workload == "simdisk":
+        run_simdisk(args)
     else:
         run_gpu(args)
 

@@ -79,6 +79,7 @@ typedef struct fs_code fs_code; /* opaque; owned by the library */
 #define FS_OP_DECODE 1
 #define FS_OP_UPDATE 2
 #define FS_OP_REPAIR 3
+#define FS_OP_SCHEDULE 4 /* fs_batch only: the decoding schedule alone (Algorithm 5) */
 
 #define FS_WS_STATUS_OFFSET 0 /* int32 device status word inside every workspace */
 
@@ -365,7 +366,11 @@ typedef struct {
 
 typedef struct fs_batch fs_batch; /* opaque; owned by the library */
 
-/* Plans a batch of n stripes for op (FS_OP_ENCODE or FS_OP_DECODE): checks
+/* Plans a batch of n stripes for op (FS_OP_ENCODE, FS_OP_DECODE, or
+ * FS_OP_SCHEDULE: the decoding schedule of every stripe without its payload,
+ * for symbolic sweeps over erasure patterns such as the paper's simDisk
+ * utility; it fills d_unrecovered, d_n_unrecovered and the path in d_ws, and
+ * d_coded / d_data_out may be NULL): checks
  * every stripe (FS_ERR_INVALID on the first bad one, nothing created),
  * copies the per-stripe launch arguments to device memory (this call
  * allocates; the run does not). The stripes' buffers and codes must outlive

@@ -27,8 +27,10 @@ bool stripe_ok(const fs_stripe &s, int op, int device) {
         if ((c->m > 0) != (s.d_parity != nullptr)) return false;
         return aligned16(s.d_data) && aligned16(s.d_parity) && aligned16(s.d_coded);
     }
-    if (!s.d_data_out || !s.d_unrecovered || !s.d_n_unrecovered || !s.d_ws) return false;
-    if (c->n > 0 && (!s.d_coded || !s.d_erased)) return false;
+    if (!s.d_unrecovered || !s.d_n_unrecovered || !s.d_ws) return false;
+    if (c->n > 0 && !s.d_erased) return false;
+    if (op == FS_OP_SCHEDULE) return aligned16(s.d_ws);
+    if (!s.d_data_out || (c->n > 0 && !s.d_coded)) return false;
     return aligned16(s.d_coded) && aligned16(s.d_data_out) && aligned16(s.d_ws);
 }
 
@@ -37,7 +39,8 @@ bool stripe_ok(const fs_stripe &s, int op, int device) {
 FS_API fs_status fs_batch_create(const fs_stripe *stripes, int32_t n, int op, fs_batch **out) {
     if (!out) return FS_ERR_INVALID;
     *out = nullptr;
-    if (n < 0 || (n > 0 && !stripes) || (op != FS_OP_ENCODE && op != FS_OP_DECODE))
+    if (n < 0 || (n > 0 && !stripes) ||
+        (op != FS_OP_ENCODE && op != FS_OP_DECODE && op != FS_OP_SCHEDULE))
         return FS_ERR_INVALID;
     int device = -1;
     if (cudaGetDevice(&device) != cudaSuccess) return FS_ERR_CUDA;
@@ -69,7 +72,7 @@ FS_API fs_status fs_batch_create(const fs_stripe *stripes, int32_t n, int op, fs
     cudaError_t e = op == FS_OP_ENCODE
                         ? encode_batch_plan(codes.data(), cin.data(), a.data(), b.data(), n, &bt->enc)
                         : decode_batch_plan(codes.data(), cin.data(), er.data(), c.data(), un.data(),
-                                            nu.data(), w.data(), n, &bt->dec);
+                                            nu.data(), w.data(), n, op == FS_OP_SCHEDULE, &bt->dec);
     if (e != cudaSuccess) {
         delete bt;
         return e == cudaErrorMemoryAllocation ? FS_ERR_NOMEM

@@ -113,7 +113,7 @@ struct DecodeBatch;
 cudaError_t decode_batch_plan(const fs_code *const *codes, const void *const *coded,
                               const uint8_t *const *erased, void *const *data_out,
                               uint8_t *const *unrecovered, int32_t *const *n_unrecovered,
-                              void *const *ws, int32_t n, DecodeBatch **out);
+                              void *const *ws, int32_t n, bool schedule_only, DecodeBatch **out);
 cudaError_t decode_batch_run(const DecodeBatch *b, cudaStream_t s);
 void decode_batch_free(DecodeBatch *b);
 void free_slice_tables(fs_code *c);

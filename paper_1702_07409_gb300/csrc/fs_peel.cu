@@ -1104,7 +1104,7 @@ cudaError_t upload_vec(T **dst, const std::vector<T> &v) {
 cudaError_t decode_batch_plan(const fs_code *const *codes, const void *const *coded,
                               const uint8_t *const *erased, void *const *data_out,
                               uint8_t *const *unrecovered, int32_t *const *n_unrecovered,
-                              void *const *ws, int32_t n, DecodeBatch **out) {
+                              void *const *ws, int32_t n, bool schedule_only, DecodeBatch **out) {
     *out = nullptr;
     std::vector<DpgArgs> dc, dg;
     std::vector<DpgCompactPlace> pc;
@@ -1127,6 +1127,7 @@ cudaError_t decode_batch_plan(const fs_code *const *codes, const void *const *co
             pg.push_back(pl);
             b->smem_g = std::max(b->smem_g, (int)pl.bytes);
         }
+        if (schedule_only) continue;  // the symbolic pass alone
         const PeelArgs pa = peel_args(c, static_cast<const uint4 *>(coded[i]),
                                       static_cast<uint4 *>(data_out[i]), w);
         peel.push_back(pa);
@@ -1152,7 +1153,7 @@ cudaError_t decode_batch_plan(const fs_code *const *codes, const void *const *co
                                  b->smem_c);
     if (e == cudaSuccess && b->smem_g > 48 * 1024)
         e = cudaFuncSetAttribute(k_dpg_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, b->smem_g);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && b->n_items > 0)
         e = cudaFuncSetAttribute(k_peel_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)b->smem_p);
     if (e != cudaSuccess) {

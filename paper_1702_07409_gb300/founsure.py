@@ -19,6 +19,7 @@ FS_OK, FS_STALL, FS_ERR_INVALID, FS_ERR_CUDA, FS_ERR_NOMEM, FS_ERR_TIMEOUT, FS_E
 ENCODE_STATIC_SCRATCH_BYTES = 65536
 DECODE_JOINT, DECODE_TWO_PASS = 0, 1
 OP_ENCODE, OP_DECODE, OP_UPDATE, OP_REPAIR = 0, 1, 2, 3
+OP_SCHEDULE = 4  # batches only: the decoding schedule without its payload
 TUNE_PEEL_CTAS, TUNE_GATHER_CTAS, TUNE_DPG_COMPACT, TUNE_L2_HINTS = 1, 2, 3, 4
 TUNE_ENCODE_SLICES = 5
 TUNE_ROWS_PER_TICKET = 6
@@ -318,10 +319,11 @@ class Code:
 class Batch:
     """fs_batch: many stripes (each with its own Code) encoded or decoded in a
     fixed number of launches. `stripes` is a list of dicts with the fs_stripe
-    fields as tensors: encode {code, data, parity, coded}; decode {code,
-    coded, erased, data_out, unrecovered, n_unrecovered, ws}. The tensors are
-    kept alive by the batch; run() only enqueues (capturable in a CUDA
-    graph)."""
+    fields as tensors (or device addresses): encode {code, data, parity,
+    coded}; decode {code, coded, erased, data_out, unrecovered, n_unrecovered,
+    ws}; schedule (OP_SCHEDULE) {code, erased, unrecovered, n_unrecovered,
+    ws}. The tensors are kept alive by the batch; run() only enqueues
+    (capturable in a CUDA graph)."""
 
     def __init__(self, stripes, op: int):
         self._keep = stripes
@@ -335,6 +337,8 @@ class Batch:
             elif op == OP_DECODE:  # other ops are left to the library to reject
                 code._need(s["coded"], code.n * code.t, "coded")
                 code._need(s["data_out"], code.b * code.t, "data_out")
+                code._need(s["ws"], code.workspace_bytes(OP_DECODE), "ws")
+            elif op == OP_SCHEDULE:
                 code._need(s["ws"], code.workspace_bytes(OP_DECODE), "ws")
             arr[i] = _Stripe(code._h, _addr(s.get("data")), _addr(s.get("parity")),
                              _addr(s.get("coded")), _addr(s.get("erased")),

@@ -405,3 +405,38 @@ def test_column_payload_without_its_plan_reports_invalid():
     assert fs.Code.ws_status(ws2) == fs.FS_OK
     want, _ = oracle.decode(case.g, _host(cd), _host(er), case.t)
     assert np.array_equal(_host(out), want)
+
+
+def test_code_extension_encodes_only_the_new_rows():
+    """The paper's update (making a code stronger): e more coded blocks from
+    the same degree distribution. The generator keeps the first n rows when
+    n grows, so the extended code is the old one plus rows n..n+e-1, and
+    fs_encode_rows computes just those from the resident data; the old coded
+    blocks stay as they are, and the extended code decodes erasures the old
+    one could not."""
+    import torch
+    fs = _fs()
+    b, m, n, e, t = 600, 24, 700, 200, 64
+    g = gen.make_graph(b, m, n, gen.DIST_FINITE40, stripe=9)
+    gx = gen.make_graph(b, m, n + e, gen.DIST_FINITE40, stripe=9)
+    assert np.array_equal(gx.lt_ptr[:n + 1], g.lt_ptr) and np.array_equal(gx.pre_idx, g.pre_idx)
+    data = gen.fill_bytes(gen.SEED_DATA + 9, b * t).reshape(b, t)
+    par, cod = oracle.encode(g, data, t)
+    parx, codx = oracle.encode(gx, data, t)
+    assert np.array_equal(codx[:n], cod) and np.array_equal(parx, par)
+    code_x = fs.Code(gx, t)
+    d = _dev(data)
+    p = _dev(par)
+    cd = torch.zeros((n + e, t), dtype=torch.uint8, device="cuda")
+    cd[:n] = _dev(cod)
+    code_x.encode_rows(n, n + e, d, p, cd, code_x.workspace(fs.OP_ENCODE))
+    torch.cuda.synchronize()
+    assert np.array_equal(_host(cd), codx)
+    erased = np.zeros(n + e, np.uint8)
+    erased[gen.sample_indices(n, gen.round_count(0.35, n), gen.SEED_ERASE + 9)] = 1
+    old = oracle.dpg(g, erased[:n])
+    new = oracle.dpg(gx, erased)
+    assert int(new.unrecovered.sum()) < int(old.unrecovered.sum())
+    case = Case.__new__(Case)
+    case.g, case.b, case.m, case.n, case.t, case.code, case.mode = gx, b, m, n + e, t, code_x, 0
+    _check_decode(case, codx, cd, erased)
