@@ -140,7 +140,8 @@ class ClockSampler:
 class Stripe:
     """Device-resident state of one stripe and the seeded inputs of its steps."""
 
-    def __init__(self, stripe: int, n_rounds: int, device, tuning=None, overlap=True):
+    def __init__(self, stripe: int, n_rounds: int, device, tuning=None, overlap=True,
+                 two_pass=False):
         import torch
         self.overlap = overlap
         self.side = torch.cuda.Stream(device=device)
@@ -148,7 +149,7 @@ class Stripe:
         self.fs = fs
         off = stripe << gen.STRIPE_SHIFT
         self.g = gen.make_graph(B, M, N_CODED, gen.DIST_FINITE40, stripe=stripe)
-        self.code = fs.Code(self.g, T)
+        self.code = fs.Code(self.g, T, fs.DECODE_TWO_PASS if two_pass else fs.DECODE_JOINT)
         if tuning:
             for knob, value in tuning.items():
                 self.code.set_tuning(knob, value)
@@ -305,7 +306,7 @@ def run_gpu(args):
         tuning[fs.TUNE_L2_HINTS] = 1
 
     st = Stripe(rank, max(args.steps, 1) + args.warmup, device, tuning,
-                overlap=not args.serial_schedule)
+                overlap=not args.serial_schedule, two_pass=args.two_pass)
     torch.cuda.synchronize()
 
     # warm-up; also checks the decode outcome of this erasure draw
@@ -383,6 +384,7 @@ def run_gpu(args):
                    "unrecovered": n_unrec, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "schedule_beside_encode": not args.serial_schedule,
+                   "decoding": "two-pass (LT, then precode)" if args.two_pass else "joint",
                    "tuning": {"peel_ctas": args.peel_ctas or 1,
                               "gather_ctas": args.gather_ctas or 8}},
         "ops_ms": {k: round(v, 4) for k, v in op_ms.items()},
@@ -944,6 +946,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l2-hints", action="store_true",
                     help="tuning knob: L2 evict-last / evict-first hints")
+    ap.add_argument("--two-pass", action="store_true",
+                    help="decode in the paper's two passes (LT code, then the precode) "
+                         "instead of jointly")
     ap.add_argument("--serial-schedule", action="store_true",
                     help="run the decoding schedule after the encode instead of beside it")
     ap.add_argument("--peel-ctas", type=int, default=0, help="tuning knob (1..8)")

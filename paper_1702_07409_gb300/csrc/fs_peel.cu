@@ -58,7 +58,7 @@ constexpr int kPeelThreads = 512;
 constexpr int kPeelV = 2;           // 16-byte words per payload item
 constexpr int kPeelLmax = 64;       // largest slice (words) of one payload CTA
 constexpr int kStagePairs = 256;    // pairs of one level held in shared memory
-constexpr int kStageRecipe = 2048;  // recipe entries of one level held in shared memory
+constexpr int kStageRecipe = 4096;  // recipe entries of one level held in shared memory
 constexpr int kStageLevels = 1024;  // level table entries held in shared memory
 constexpr int kStageSegs = 512;     // gather segments of one level
 constexpr int kStageMulti = 32;     // pairs with several segments in one level
