@@ -86,6 +86,12 @@ typedef struct fs_code fs_code; /* opaque; owned by the library */
 /*
  * Creates a code from its two graphs (Section 2.2, Figure 2):
  *   precode: m rows (checks) over n_cols = b data blocks, or NULL for m = 0;
+ *            or a chained precode over n_cols = k_int intermediates (the
+ *            array LDPC checks of Algorithm 2): check j's members lie below
+ *            b + j (data blocks and earlier parities; its own parity b + j is
+ *            implied), and the checks come in level order (level = 1 + the
+ *            deepest parity member). Chained codes encode level by level with
+ *            the row-gather kernels; fs_update and batched encodes reject them.
  *   lt:      n rows (coded blocks) over n_cols = k_int = b + m intermediates.
  * With precode == NULL, b is taken as lt->n_cols. block_bytes = t.
  * Validates both graphs on the host (bounds, ascending rows, sizes; empty

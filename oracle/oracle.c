@@ -74,7 +74,10 @@ static void xor_into(uint8_t *dst, const uint8_t *src, int64_t t)
 
 /*
  * Encoding, Section 2.2:
- *   (1) parity p_j = XOR of the data blocks of check j   (j < m)
+ *   (1) parity p_j = XOR of the members of check j, in order j = 0..m-1
+ *       (members are data blocks; in a chained precode such as the array
+ *       LDPC code of Algorithm 2 a member may also be an earlier parity
+ *       b + i, i < j, which is final by then)
  *   (2) coded c_j  = XOR of the intermediates of row j   (j < n)
  * parity may be NULL when m == 0. Returns 0, or -1 on a bad index.
  */
@@ -89,8 +92,8 @@ int or_encode(int32_t b, int32_t m, int32_t n,
         memset(p, 0, (size_t)t);
         for (int32_t e = pre_ptr[j]; e < pre_ptr[j + 1]; e++) {
             int32_t i = pre_idx[e];
-            if (i < 0 || i >= b) return -1;
-            xor_into(p, data + (int64_t)i * t, t);
+            if (i < 0 || i >= b + j) return -1;
+            xor_into(p, i < b ? data + (int64_t)i * t : parity + (int64_t)(i - b) * t, t);
         }
     }
     for (int32_t j = 0; j < n; j++) {

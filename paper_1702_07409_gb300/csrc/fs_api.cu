@@ -55,6 +55,7 @@ void free_code(fs_code *c) {
     cudaFree(c->con_ptr4);
     cudaFree(c->con_idx4);
     free_slice_tables(c);
+    free(c->pre_level_off);
     free(c);
 }
 
@@ -85,10 +86,29 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     if (block_bytes == 0 || (block_bytes & 15) != 0) return FS_ERR_INVALID;
     if (flags != FS_DECODE_JOINT && flags != FS_DECODE_TWO_PASS) return FS_ERR_INVALID;
     const int32_t m = precode ? precode->n_rows : 0;
-    const int32_t b = precode ? precode->n_cols : lt->n_cols;
+    // a precode over the intermediates (as many columns as the LT graph) is
+    // chained: check j may hold earlier parities b + i, i < j
+    const bool chained = precode && m > 0 && precode->n_cols == lt->n_cols;
+    const int32_t b = precode ? (chained ? precode->n_cols - m : precode->n_cols) : lt->n_cols;
     if (precode && !csr_ok(precode, -1, -1)) return FS_ERR_INVALID;
     if (b < 1 || m < 0 || (int64_t)b + m > INT32_MAX / 2) return FS_ERR_INVALID;
     if (!csr_ok(lt, -1, b + m)) return FS_ERR_INVALID;
+    // chained: each check's level is 1 + the deepest parity among its members;
+    // the checks must come in level order (each level is then one row range)
+    std::vector<int32_t> level_off;
+    if (chained) {
+        std::vector<int32_t> lvl(m, 0);
+        for (int32_t j = 0; j < m; ++j) {
+            for (int32_t e = precode->row_ptr[j]; e < precode->row_ptr[j + 1]; ++e) {
+                const int32_t v = precode->col_idx[e];
+                if (v >= b + j) return FS_ERR_INVALID;  // not an earlier intermediate
+                if (v >= b) lvl[j] = std::max(lvl[j], lvl[v - b] + 1);
+            }
+            if (j > 0 && lvl[j] < lvl[j - 1]) return FS_ERR_INVALID;
+            while ((int32_t)level_off.size() <= lvl[j]) level_off.push_back(j);
+        }
+        level_off.push_back(m);
+    }
     const int32_t n = lt->n_rows;
     const int64_t e_lt = lt->row_ptr[n];
     const int64_t e_pre = precode ? precode->row_ptr[m] : 0;
@@ -157,6 +177,17 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     c->e_pre = e_pre;
     c->e_con = e_con;
     c->max_con_deg = max_con_deg;
+    c->chained = chained ? 1 : 0;
+    c->n_pre_levels = chained ? (int32_t)level_off.size() - 1 : (m > 0 ? 1 : 0);
+    c->pre_level_off = nullptr;
+    if (chained) {
+        c->pre_level_off = (int32_t *)malloc(sizeof(int32_t) * level_off.size());
+        if (!c->pre_level_off) {
+            free(c);
+            return FS_ERR_NOMEM;
+        }
+        memcpy(c->pre_level_off, level_off.data(), sizeof(int32_t) * level_off.size());
+    }
     c->max_var_deg = max_var_deg;
     c->e_con4 = (int64_t)con_ptr4[n_con];
     c->peel_ctas = 1;
@@ -350,6 +381,7 @@ FS_API fs_status fs_update(const fs_code *c, const int32_t *d_idx, int32_t n_idx
                            const void *d_new, void *d_data, void *d_parity, void *d_coded,
                            void *d_ws, void *stream) {
     if (!c || n_idx < 0 || !d_data || !d_coded || !d_ws) return FS_ERR_INVALID;
+    if (c->chained) return FS_ERR_INVALID;  // deltas cross one precode level only
     if (n_idx > 0 && (!d_idx || !d_new)) return FS_ERR_INVALID;
     if ((c->m > 0) != (d_parity != nullptr)) return FS_ERR_INVALID;
     if (!aligned16(d_new) || !aligned16(d_data) || !aligned16(d_parity) || !aligned16(d_coded) ||

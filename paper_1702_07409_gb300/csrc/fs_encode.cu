@@ -686,7 +686,9 @@ std::vector<int> colour_edges(const std::vector<std::pair<int, int>> &edges, int
 cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t *con_idx) {
     c->sl_slots = 0;
     c->sl_parts = 0;
-    if (c->b < 1 || c->n < 1 || c->n >= kNoSlot || c->m >= kNoSlot) return cudaSuccess;
+    // a chained precode (parities over earlier parities) needs its levels in
+    // order: such codes take the row-gather encode
+    if (c->chained || c->b < 1 || c->n < 1 || c->n >= kNoSlot || c->m >= kNoSlot) return cudaSuccess;
     const int32_t box_rows = c->b < 256 ? c->b : 256;
     const int64_t bpad = ((int64_t)c->b + box_rows - 1) / box_rows * box_rows;
     // data slots, parity slots, then 8 zero slots (one per bank group)
@@ -1022,21 +1024,29 @@ cudaError_t launch_encode(const fs_code *c, const void *data, void *parity, void
     a.n_chunks = n_chunks;
     a.hints = c->l2_hints;
     if (c->m > 0) {  // step (1): parities over the data blocks
-        a.ptr = c->pre_ptr;
+        // a chained precode runs level by level: the checks of a level read
+        // parities of earlier levels only (one launch each, in stream order)
         a.idx = c->pre_idx;
         a.inA = static_cast<const uint4 *>(data);
-        a.inB = nullptr;
+        a.inB = c->chained ? static_cast<const uint4 *>(parity) : nullptr;
         a.split = c->b;
-        a.out = static_cast<uint4 *>(parity);
-        a.n_rows = c->m;
         a.stream_out = 0;
         a.rows = 1;  // check rows are long: one per ticket keeps every SM busy
         a.t0 = 0;
-        const int64_t tickets = (int64_t)n_chunks * c->m;
-        k_rows<<<grid_for(tickets, c->num_sms, ctas), kEncThreads, 0, s>>>(a, (int32_t)tickets,
-                                                                          hdr + WS_COUNT_A);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        for (int32_t l = 0; l < c->n_pre_levels; ++l) {
+            const int32_t r0 = c->chained ? c->pre_level_off[l] : 0;
+            const int32_t r1 = c->chained ? c->pre_level_off[l + 1] : c->m;
+            a.ptr = c->pre_ptr + r0;  // row pointers stay absolute into pre_idx
+            a.out = static_cast<uint4 *>(parity) + (int64_t)r0 * c->tw;
+            a.n_rows = r1 - r0;
+            if (l > 0) e = cudaMemsetAsync(hdr + WS_COUNT_A, 0, sizeof(int32_t), s);
+            if (e != cudaSuccess) return e;
+            const int64_t tickets = (int64_t)n_chunks * a.n_rows;
+            k_rows<<<grid_for(tickets, c->num_sms, ctas), kEncThreads, 0, s>>>(a, (int32_t)tickets,
+                                                                              hdr + WS_COUNT_A);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
     }
     if (c->n > 0) {  // step (2): coded rows over data blocks and parities
         a.ptr = c->con_ptr;

@@ -35,6 +35,9 @@ struct fs_code {
     int64_t tw;           // block size in 16-byte words
     int flags;
     int64_t e_lt, e_pre, e_con;
+    int chained;          // 1: precode members are intermediates (check j's below b + j)
+    int32_t n_pre_levels; // chained: levels of parities (level = 1 + deepest parity member)
+    int32_t *pre_level_off;  // chained, host: first check of each level (rows in level order)
     int32_t max_con_deg;  // largest constraint degree
     int32_t max_var_deg;  // largest number of constraints containing one var
     // device arrays

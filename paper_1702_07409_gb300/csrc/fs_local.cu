@@ -126,7 +126,7 @@ int32_t run_cga(int32_t k, const fs_csr *lt, int32_t max_sweeps, std::vector<Set
 
 void build_groups(fs_local *o, const fs_csr *precode, const fs_csr *lt, int32_t max_sweeps) {
     const int32_t n = lt->n_rows, k = o->k_int;
-    const int32_t b = precode ? precode->n_cols : k;
+    const int32_t b = k - (precode ? precode->n_rows : 0);  // data blocks (plain or chained precode)
     std::vector<Set> B, L;
     o->sweeps = run_cga(k, lt, max_sweeps, B, L);
     std::vector<int32_t> c2_col(k, -1);  // first column reduced to {i}
@@ -475,7 +475,8 @@ FS_API fs_status fs_local_create(const fs_csr *precode, const fs_csr *lt, int32_
     *out = nullptr;
     if (flags != 0 && flags != FS_LOCAL_HOST_ONLY) return FS_ERR_INVALID;
     const int32_t m = precode ? precode->n_rows : 0;
-    const int32_t b = precode ? precode->n_cols : lt->n_cols;
+    const bool chained = precode && m > 0 && precode->n_cols == lt->n_cols;  // as fs_code_create
+    const int32_t b = precode ? (chained ? precode->n_cols - m : precode->n_cols) : lt->n_cols;
     if (precode && !csr_ok(precode, -1, -1)) return FS_ERR_INVALID;
     if (b < 1 || m < 0 || (int64_t)b + m > INT32_MAX / 2) return FS_ERR_INVALID;
     if (!csr_ok(lt, -1, b + m)) return FS_ERR_INVALID;

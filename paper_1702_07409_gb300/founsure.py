@@ -172,7 +172,9 @@ class Code:
     """A Founsure code on the current CUDA device (fs_code_create).
 
     ``graph`` is any object with b, m, n, pre_ptr, pre_idx, lt_ptr, lt_idx
-    (e.g. ``gen.Graph``); ``block_bytes`` is t (a multiple of 16)."""
+    (e.g. ``gen.Graph``; ``chained=True`` marks a precode over the
+    intermediates, such as the array LDPC checks); ``block_bytes`` is t (a
+    multiple of 16)."""
 
     def __init__(self, graph, block_bytes: int, mode: int = DECODE_JOINT):
         import torch
@@ -188,7 +190,8 @@ class Code:
             pp = np.ascontiguousarray(graph.pre_ptr, np.int32)
             pi = np.ascontiguousarray(graph.pre_idx, np.int32)
             self._keep += [pp, pi]
-            pre = _Csr(self.m, self.b, pp.ctypes.data, pi.ctypes.data if pi.size else None)
+            pre = _Csr(self.m, self.k_int if getattr(graph, "chained", False) else self.b,
+                       pp.ctypes.data, pi.ctypes.data if pi.size else None)
         lp = np.ascontiguousarray(graph.lt_ptr, np.int32)
         li = np.ascontiguousarray(graph.lt_idx, np.int32)
         self._keep += [lp, li]
@@ -398,7 +401,8 @@ class Local:
             pp = np.ascontiguousarray(graph.pre_ptr, np.int32)
             pi = np.ascontiguousarray(graph.pre_idx, np.int32)
             self._keep += [pp, pi]
-            pre = _Csr(self.m, self.b, pp.ctypes.data, pi.ctypes.data if pi.size else None)
+            pre = _Csr(self.m, self.k_int if getattr(graph, "chained", False) else self.b,
+                       pp.ctypes.data, pi.ctypes.data if pi.size else None)
         lp = np.ascontiguousarray(graph.lt_ptr, np.int32)
         li = np.ascontiguousarray(graph.lt_idx, np.int32)
         self._keep += [lp, li]

@@ -148,7 +148,9 @@ def precode_graph(b: int, m: int, q: int, seed: int):
 class Graph:
     """A Founsure code graph: m precode checks over b data blocks (CSR, rows =
     checks) and n LT rows over k_int = b + m intermediates (CSR, rows = coded
-    blocks). Intermediates are data 0..b-1 followed by parities b..b+m-1."""
+    blocks). Intermediates are data 0..b-1 followed by parities b..b+m-1.
+    chained: the precode's members are intermediates, check j's below b + j
+    (its own parity b + j is not listed), as in the array LDPC precode."""
     b: int
     m: int
     n: int
@@ -156,6 +158,7 @@ class Graph:
     pre_idx: np.ndarray
     lt_ptr: np.ndarray
     lt_idx: np.ndarray
+    chained: bool = False
 
     @property
     def k_int(self) -> int:
@@ -183,6 +186,52 @@ def make_graph(b: int, m: int, n: int, dist: int, c: float = 0.0, delta: float =
         pp, pi = np.zeros(1, dtype=np.int32), np.zeros(0, dtype=np.int32)
     lp, li = lt_graph(k_int, n, mu, dmax, seed_graph + off)
     return Graph(b, m, n, pp, pi, lp, li)
+
+
+def largest_prime_factor(x: int) -> int:
+    f, best = 2, 1
+    while f * f <= x:
+        while x % f == 0:
+            best, x = f, x // f
+        f += 1
+    return x if x > 1 else best
+
+
+def array_precode(b: int, k: int):
+    """The array LDPC checks (check #1) of Algorithm 2 for b data blocks and k
+    intermediates: p = the largest prime factor of k, k' = k / p,
+    j' = k' - b / p. Check r = i + j p (j < j', i < p) has the k' - j'
+    members
+        k' p - (j' - j + m - 1) p - ((m (j' - j - 1) - i - 1 + p) mod p) - 1,
+    m = 1 .. k' - j', and its parity is intermediate b + r. The members of the
+    checks of block j are data blocks and parities of blocks j-1, j-2, ...,
+    so the parities are computed block by block. Returns the CSR (ptr, idx)
+    of the m = k - b checks, members ascending. Needs p | b and 1 <= j' < k'."""
+    p = largest_prime_factor(k)
+    kp = k // p
+    if k < 2 or b <= 0 or b % p or not (1 <= kp - b // p < kp):
+        raise ValueError("no array LDPC code for b=%d, k=%d (p=%d)" % (b, k, p))
+    jp = kp - b // p
+    rows = []
+    for j in range(jp):
+        for i in range(p):
+            rows.append(sorted(kp * p - (jp - j + mm - 1) * p - ((mm * (jp - j - 1) - i - 1 + p) % p) - 1
+                               for mm in range(1, kp - jp + 1)))
+    ptr = np.zeros(len(rows) + 1, np.int32)
+    for r, row in enumerate(rows):
+        ptr[r + 1] = ptr[r] + len(row)
+    return ptr, np.array([v for row in rows for v in row], dtype=np.int32)
+
+
+def make_graph_array(b: int, k: int, n: int, dist: int, c: float = 0.0, delta: float = 0.0,
+                     stripe: int = 0, seed_graph: int = SEED_GRAPH) -> Graph:
+    """A graph with the array LDPC precode of Algorithm 2 (k - b chained
+    checks) and LT rows over the k intermediates drawn as in make_graph."""
+    off = stripe << STRIPE_SHIFT
+    mu, dmax, _ = pmf(dist, k, c, delta)
+    pp, pi = array_precode(b, k)
+    lp, li = lt_graph(k, n, mu, dmax, seed_graph + off)
+    return Graph(b, k - b, n, pp, pi, lp, li, chained=True)
 
 
 def n_for_rate(k: int) -> int:

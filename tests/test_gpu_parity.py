@@ -440,3 +440,73 @@ def test_code_extension_encodes_only_the_new_rows():
     case = Case.__new__(Case)
     case.g, case.b, case.m, case.n, case.t, case.code, case.mode = gx, b, m, n + e, t, code_x, 0
     _check_decode(case, codx, cd, erased)
+
+
+@pytest.mark.parametrize("t", [48, 4096 + 16])
+def test_array_precode_encode_decode(t):
+    """The array LDPC precode of Algorithm 2 (b = 4154, k = 4288: p = 67, two
+    levels of 67 checks, the second reading parities of the first) under an
+    LT code of n = 5574: the level-by-level encode and the joint decode are
+    bit-exact against the oracle; the delta update and batched encodes reject
+    the chained code."""
+    import torch
+    fs = _fs()
+    b, k, n = 4154, 4288, 5574
+    g = gen.make_graph_array(b, k, n, gen.DIST_FINITE40)
+    m = k - b
+    data = gen.fill_bytes(gen.SEED_DATA + 5, b * t).reshape(b, t)
+    code = fs.Code(g, t)
+    d = _dev(data)
+    p = torch.empty((m, t), dtype=torch.uint8, device="cuda")
+    cd = torch.empty((n, t), dtype=torch.uint8, device="cuda")
+    code.encode(d, p, cd, code.workspace(fs.OP_ENCODE))
+    torch.cuda.synchronize()
+    par, cod = oracle.encode(g, data, t)
+    assert np.array_equal(_host(p), par) and np.array_equal(_host(cd), cod)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cd.zero_()
+    code.encode_static(d, p, cd, st)
+    torch.cuda.synchronize()
+    assert np.array_equal(_host(cd), cod)
+    case = Case.__new__(Case)
+    case.g, case.b, case.m, case.n, case.t, case.code, case.mode = g, b, m, n, t, code, 0
+    path = _check_decode(case, cod, cd, _erased(n, 0.15, gen.SEED_ERASE + 5))
+    assert path.n_pairs > 0
+    with pytest.raises(fs.FounsureError):
+        code.update(_dev(np.array([0], np.int32)), 1, d[:1].clone(), d, p, cd,
+                    code.workspace(fs.OP_UPDATE, 1))
+    with pytest.raises(fs.FounsureError):
+        fs.Batch([{"code": code, "data": d, "parity": p, "coded": cd}], fs.OP_ENCODE)
+    out = torch.empty((b, t), dtype=torch.uint8, device="cuda")
+    dec = fs.Batch([{"code": code, "coded": cd, "erased": _dev(_erased(n, 0.15, gen.SEED_ERASE + 5)),
+                     "data_out": out, "unrecovered": torch.empty(k, dtype=torch.uint8, device="cuda"),
+                     "n_unrecovered": torch.empty(1, dtype=torch.int32, device="cuda"),
+                     "ws": code.workspace(fs.OP_DECODE)}], fs.OP_DECODE)
+    dec.run()
+    torch.cuda.synchronize()
+    want, _ = oracle.decode(g, cod, _erased(n, 0.15, gen.SEED_ERASE + 5), t)
+    assert np.array_equal(_host(out), want)
+
+
+def test_chained_precode_validation():
+    """A chained check may read only earlier parities, and the checks must
+    come in level order."""
+    fs = _fs()
+    lt = [[0], [1], [2], [3], [4], [5], [0, 4]]
+
+    def graph(checks):
+        ptr = np.zeros(len(checks) + 1, np.int32)
+        for j, r in enumerate(checks):
+            ptr[j + 1] = ptr[j] + len(r)
+        idx = np.array([v for r in checks for v in r], np.int32)
+        lp = np.zeros(len(lt) + 1, np.int32)
+        for j, r in enumerate(lt):
+            lp[j + 1] = lp[j] + len(r)
+        return gen.Graph(3, len(checks), len(lt), ptr, idx, lp,
+                         np.array([v for r in lt for v in r], np.int32), chained=True)
+
+    fs.Code(graph([[0, 1], [2, 3], [1, 3, 4]]), 16).close()  # levels 0, 1, 2
+    with pytest.raises(fs.FounsureError):
+        fs.Code(graph([[0, 1], [2, 4], [1, 2]]), 16)  # check 1 reads its own parity
+    with pytest.raises(fs.FounsureError):
+        fs.Code(graph([[0, 1], [2, 3], [1, 2]]), 16)  # level 1 before level 0
