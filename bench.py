@@ -829,6 +829,127 @@ def run_simdisk(args):
         print(json.dumps(line), flush=True)
 
 
+def run_array(args):
+    """The array LDPC precode of Algorithm 2 at a size like the precoded
+    stripe: b = 4154 data blocks of 64 KiB, k = 4288 intermediates (p = 67,
+    k' = 64, j' = 2: 134 checks in two levels, the second reading parities of
+    the first), n = 5574 = 1.3 k coded blocks, FiniteDist max-degree-40, 20%
+    erased. One step = encode (one row-gather launch per precode level, then
+    the LT rows) + decode (schedule beside nothing: serial, then payload).
+    The delta update does not apply to chained precodes. cpu_baseline: the
+    oracle's encode + decode on a 16 KiB slice of every block."""
+    import torch
+    from paper_1702_07409_gb300 import founsure as fs
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    peak, peak_kind = peaks()
+    b, k = 4154, 4288
+    n, m = (13 * k + 5) // 10, k - b
+    g = gen.make_graph_array(b, k, n, gen.DIST_FINITE40)
+    code = fs.Code(g, T)
+    gen_t = torch.Generator(device=device)
+    gen_t.manual_seed(gen.SEED_DATA + rank)
+    data = torch.randint(0, 256, (b, T), dtype=torch.uint8, device=device, generator=gen_t)
+    par = torch.empty((m, T), dtype=torch.uint8, device=device)
+    coded = torch.empty((n, T), dtype=torch.uint8, device=device)
+    er = np.zeros(n, np.uint8)
+    er[gen.sample_indices(n, gen.round_count(ERASE_FRAC, n), gen.SEED_ERASE)] = 1
+    d_er = torch.from_numpy(er).to(device)
+    out = torch.empty((b, T), dtype=torch.uint8, device=device)
+    unrec = torch.empty(k, dtype=torch.uint8, device=device)
+    nun = torch.empty(1, dtype=torch.int32, device=device)
+    ews, dws = code.workspace(fs.OP_ENCODE), code.workspace(fs.OP_DECODE)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step(record=False):
+        if record:
+            evs[0].record()
+        code.encode(data, par, coded, ews)
+        if record:
+            evs[1].record()
+        code.decode_schedule(d_er, unrec, nun, dws)
+        if record:
+            evs[2].record()
+        code.decode_payload(coded, out, dws)
+        if record:
+            evs[3].record()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    un = unrec[:b].bool()
+    if not torch.equal(out[~un], data[~un]):
+        raise RuntimeError("array-precoded decode differs from the data")
+    recovered = int((~un).sum().item())
+    view = code.decode_path(dws)
+    g_arr = view["pair_g"].cpu().numpy()
+    coded_pairs = int((g_arr < n).sum())
+    K = args.steps
+    t_enc, t_sch, t_pay = [], [], []
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0.record()
+        for _ in range(K):
+            step(record=True)
+            torch.cuda.synchronize()
+            t_enc.append(evs[0].elapsed_time(evs[1]))
+            t_sch.append(evs[1].elapsed_time(evs[2]))
+            t_pay.append(evs[2].elapsed_time(evs[3]))
+        t1.record()
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    enc_ms, sch_ms, pay_ms = (statistics.mean(x) for x in (t_enc, t_sch, t_pay))
+    ms = enc_ms + sch_ms + pay_ms
+    src = (b + recovered) * T
+    enc_bytes = (b + m + n) * T
+    pay_bytes = (coded_pairs + recovered) * T
+
+    import oracle  # cpu_baseline leg
+    oracle.build()
+    ts = args.cpu_slice
+    hdata = gen.fill_bytes(gen.SEED_DATA, b * ts).reshape(b, ts)
+    c0 = time.perf_counter()
+    _, hcod = oracle.encode(g, hdata, ts)
+    hout, hpath = oracle.decode(g, hcod, er, ts)
+    cpu_s = time.perf_counter() - c0
+    cpu_src = (b + int((hpath.unrecovered[:b] == 0).sum())) * ts
+    line = {
+        "metric": METRIC + " (array LDPC precode)", "value": round(src / (ms * 1e-3) / 1e9, 2),
+        "unit": "GB/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
+        "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded device random bytes, splitmix64 LT graph, Algorithm 2 precode)",
+        "config": {"workload": "array LDPC precode b=4154 x 64 KiB, k=4288 (p=67, two levels of 67 "
+                               "checks), n=5574, FiniteDist max-degree-40, 20% erased; step = "
+                               "encode + decode (schedule, payload), serial",
+                   "unrecovered": int(unrec.sum().item()),
+                   "l2": "inputs larger than L2 (no flush)"},
+        "ops_ms": {"encode": round(enc_ms, 4), "decode_schedule": round(sch_ms, 4),
+                   "decode_payload": round(pay_ms, 4)},
+        "roofline": {"bound": "hbm", "kernel": "k_peel (fs_decode_payload)",
+                     "achieved": round(pay_bytes / (pay_ms * 1e-3) / 1e9, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(pay_bytes / (pay_ms * 1e-3) / 1e9 / peak, 4), "traffic": None,
+                     "algorithmic_bytes": pay_bytes},
+        "encode_roofline": {"bound": "hbm", "kernel": "k_rows (fs_encode, one launch per precode "
+                                                      "level + the LT rows)",
+                            "achieved": round(enc_bytes / (enc_ms * 1e-3) / 1e9, 1), "peak": peak,
+                            "unit": "GB/s",
+                            "frac": round(enc_bytes / (enc_ms * 1e-3) / 1e9 / peak, 4),
+                            "traffic": None, "algorithmic_bytes": enc_bytes},
+        "cpu_baseline": {"value": round(cpu_src / cpu_s / 1e9, 4), "unit": "GB/s", "cores": 1,
+                         "kind": "oracle", "sample": "encode + decode of the same code and "
+                                                     "erasures on a %d-byte slice of every block" % ts},
+        # per step: the precode's two levels and the LT rows, the schedule, the payload
+        "gpu_launches": 5 * K,
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                   "reasons": clocks["reasons"]},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_serving(args):
     """Requests served from device-resident stripes (paper_1702_07409_gb300.serve):
     Poisson arrivals (mean 2000 requests/s, seeded exponential gaps) of encode
@@ -955,12 +1076,13 @@ def main():
     ap.add_argument("--gather-ctas", type=int, default=0, help="tuning knob (1..16)")
 
     ap.add_argument("--workload", default="stripe",
-                    choices=["stripe", "batched", "serving", "repair_local", "simdisk"],
+                    choices=["stripe", "batched", "serving", "repair_local", "simdisk", "array"],
                     help="stripe: the precoded stripe step (default); batched: many uneven "
                          "stripes through fs_batch vs per-stripe calls; serving: a Poisson "
                          "stream of requests on resident stripes; repair_local: repair of 5%% "
                          "lost coded blocks from local recovery groups; simdisk: every "
-                         "combination of 1-4 failed disks out of 10, symbolic decodes")
+                         "combination of 1-4 failed disks out of 10, symbolic decodes; array: "
+                         "the array LDPC precode of Algorithm 2")
     ap.add_argument("--requests", type=int, default=2000, help="requests of --workload serving")
     ap.add_argument("--rate", type=float, default=2000.0, help="mean arrivals per second (serving)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="HBM budget (serving)")
@@ -981,6 +1103,8 @@ def main():
         run_repair_local(args)
     elif args.workload == "simdisk":
         run_simdisk(args)
+    elif args.workload == "array":
+        run_array(args)
     else:
         run_gpu(args)
 
