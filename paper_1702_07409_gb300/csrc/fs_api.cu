@@ -381,7 +381,6 @@ FS_API fs_status fs_update(const fs_code *c, const int32_t *d_idx, int32_t n_idx
                            const void *d_new, void *d_data, void *d_parity, void *d_coded,
                            void *d_ws, void *stream) {
     if (!c || n_idx < 0 || !d_data || !d_coded || !d_ws) return FS_ERR_INVALID;
-    if (c->chained) return FS_ERR_INVALID;  // deltas cross one precode level only
     if (n_idx > 0 && (!d_idx || !d_new)) return FS_ERR_INVALID;
     if ((c->m > 0) != (d_parity != nullptr)) return FS_ERR_INVALID;
     if (!aligned16(d_new) || !aligned16(d_data) || !aligned16(d_parity) || !aligned16(d_coded) ||

@@ -211,10 +211,14 @@ __device__ __forceinline__ int list_changed(const UpdArgs &a, const int32_t *mem
 }
 
 // changed parity j ^= XOR of the deltas of its changed members; pdelta_j
-// keeps that XOR; the chunk-0 tile of check j also lists the coded rows that
-// contain parity b + j. Tiles (listed check, chunk), chunk-major.
+// keeps that XOR; the chunk-0 tile of check j also lists the constraints
+// that contain parity b + j (coded rows, and in a chained precode the later
+// checks that read it). Only listed checks j in [j0, j1) (one precode level)
+// are taken: a chained precode runs one launch per level, so every parity a
+// check reads has its delta before the check does. Tiles (listed check,
+// chunk), chunk-major.
 __global__ void __launch_bounds__(kGatherThreads, 3)
-k_update_parity(UpdArgs a, int32_t n_chunks) {
+k_update_parity(UpdArgs a, int32_t n_chunks, int32_t j0, int32_t j1) {
     __shared__ const uint4 *s_src[kSrcBatch];
     __shared__ int s_n, s_ok;
     if (threadIdx.x == 0) s_ok = upd_ok(a);  // one decision for the whole CTA
@@ -225,12 +229,13 @@ k_update_parity(UpdArgs a, int32_t n_chunks) {
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int32_t chunk = (int32_t)(tile / np);
         const int32_t j = a.plist[tile - (int64_t)chunk * np];
+        if (j < j0 || j >= j1) continue;  // another level's check (uniform over the CTA)
         const int32_t e0 = a.pre_ptr[j], e1 = a.pre_ptr[j + 1];
         const int64_t w0 = (int64_t)chunk * kChunkW, w1 = min(w0 + kChunkW, a.tw);
         if (chunk == 0) {
             const int32_t v = a.b + j;
             for (int32_t e = a.var_ptr[v] + threadIdx.x; e < a.var_ptr[v + 1]; e += blockDim.x)
-                touch(a, a.var_idx[e], true);
+                touch(a, a.var_idx[e], false);
         }
         uint4 acc[kWpt];
 #pragma unroll
@@ -339,9 +344,11 @@ cudaError_t launch_update(const fs_code *c, const int32_t *idx, int32_t n_idx, c
         const int32_t n_chunks = chunks_of(c->tw);
         k_update_delta<<<grid_for((int64_t)n_idx * n_chunks, c->num_sms), kGatherThreads, 0, s>>>(
             a, n_chunks);
-        if (c->m > 0) {
+        for (int32_t l = 0; l < c->n_pre_levels; ++l) {  // one level of checks per launch
+            const int32_t j0 = c->chained ? c->pre_level_off[l] : 0;
+            const int32_t j1 = c->chained ? c->pre_level_off[l + 1] : c->m;
             k_update_parity<<<grid_for((int64_t)n_chunks * c->m, c->num_sms), kGatherThreads, 0, s>>>(
-                a, n_chunks);
+                a, n_chunks, j0, j1);
         }
         if (c->n > 0)
             k_update_coded<<<grid_for((int64_t)n_chunks * c->n, c->num_sms), kGatherThreads, 0, s>>>(

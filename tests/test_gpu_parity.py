@@ -447,8 +447,8 @@ def test_array_precode_encode_decode(t):
     """The array LDPC precode of Algorithm 2 (b = 4154, k = 4288: p = 67, two
     levels of 67 checks, the second reading parities of the first) under an
     LT code of n = 5574: the level-by-level encode and the joint decode are
-    bit-exact against the oracle; the delta update and batched encodes reject
-    the chained code."""
+    bit-exact against the oracle, and so is a delta update (parity levels in
+    order); batched encodes reject the chained code."""
     import torch
     fs = _fs()
     b, k, n = 4154, 4288, 5574
@@ -472,9 +472,19 @@ def test_array_precode_encode_decode(t):
     case.g, case.b, case.m, case.n, case.t, case.code, case.mode = g, b, m, n, t, code, 0
     path = _check_decode(case, cod, cd, _erased(n, 0.15, gen.SEED_ERASE + 5))
     assert path.n_pairs > 0
-    with pytest.raises(fs.FounsureError):
-        code.update(_dev(np.array([0], np.int32)), 1, d[:1].clone(), d, p, cd,
-                    code.workspace(fs.OP_UPDATE, 1))
+    # the delta update runs the parity levels in order: rewrite 2% of the data
+    u = gen.round_count(0.02, b)
+    idx = gen.sample_indices(b, u, gen.SEED_UPDATE + 5)
+    new = gen.fill_bytes(gen.SEED_NEWDATA + 5, u * t).reshape(u, t)
+    cd.copy_(_dev(cod))
+    code.update(_dev(idx.astype(np.int32)), u, _dev(new), d, p, cd, code.workspace(fs.OP_UPDATE, u))
+    d2, par2, cod2 = oracle.update(g, data, idx, new, t)
+    torch.cuda.synchronize()
+    assert np.array_equal(_host(d), d2) and np.array_equal(_host(p), par2)
+    assert np.array_equal(_host(cd), cod2)
+    d.copy_(_dev(data))
+    p.copy_(_dev(par))
+    cd.copy_(_dev(cod))
     with pytest.raises(fs.FounsureError):
         fs.Batch([{"code": code, "data": d, "parity": p, "coded": cd}], fs.OP_ENCODE)
     out = torch.empty((b, t), dtype=torch.uint8, device="cuda")

@@ -93,14 +93,13 @@ def test_random_code(seed):
         assert np.array_equal(host(cl), want_l)
         assert np.array_equal(host(unr), lpath.unrepaired)
         assert loc.path(lws) == lpath.levels()
-    # update (plain and data-only precodes)
-    if not getattr(g, "chained", False):
-        u = int(rng.integers(0, b + 1))
-        idx = gen.sample_indices(b, u, gen.SEED_UPDATE + seed)
-        new = gen.fill_bytes(gen.SEED_NEWDATA + seed, u * t).reshape(u, t)
-        code.update(dev(idx.astype(np.int32)), u, dev(new), d, p, cd, code.workspace(fs.OP_UPDATE, u))
-        d2, par2, cod2 = oracle.update(g, data, idx, new, t)
-        torch.cuda.synchronize()
-        assert np.array_equal(host(d), d2) and np.array_equal(host(cd), cod2)
-        if m:
-            assert np.array_equal(host(p), par2)
+    # update (every precode kind)
+    u = int(rng.integers(0, b + 1))
+    idx = gen.sample_indices(b, u, gen.SEED_UPDATE + seed)
+    new = gen.fill_bytes(gen.SEED_NEWDATA + seed, u * t).reshape(u, t)
+    code.update(dev(idx.astype(np.int32)), u, dev(new), d, p, cd, code.workspace(fs.OP_UPDATE, u))
+    d2, par2, cod2 = oracle.update(g, data, idx, new, t)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(d), d2) and np.array_equal(host(cd), cod2)
+    if m:
+        assert np.array_equal(host(p), par2)
