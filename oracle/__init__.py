@@ -24,10 +24,10 @@ follows:
 * :func:`local_path` / :func:`repair_local` - repair of lost coded blocks by
   peeling over the check #3 groups, level by level like Algorithm 5.
 
-Readings of the paper: see the header of ``oracle.c``. Parity of the decoding
-*schedule* (which g decodes which f, level by level) rests only on the stated
-tie-break (lowest original degree, then lowest constraint index): parity
-unpinned beyond agreement between the oracle and the CUDA path.
+Readings of the paper: see the header of ``oracle.c``. The decoding
+*schedule* (which g decodes which f, level by level) follows from the stated
+tie-break (lowest original degree, then lowest constraint index); the tests
+check every level of it against the rules with a checker of their own.
 """
 from __future__ import annotations
 
