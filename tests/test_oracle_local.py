@@ -212,3 +212,30 @@ def test_repair_recovers_the_stored_blocks(frac):
     assert np.array_equal(out[ok], coded[ok])
     assert not out[path.unrepaired.astype(bool)].any()
     assert path.n_pairs == int(lost.sum()) - len(left) > 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_repair_schedule_obeys_the_rules(seed):
+    """Random groups and lost sets: every level is exactly the set of lost
+    blocks that some group with one unknown names (against the state at the
+    level start), each from its smallest (cardinality, index) such group, and
+    the unrepaired blocks are the lost blocks no level reached."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(20, 120))
+    groups = [tuple(sorted(rng.choice(n, size=int(rng.integers(2, 9)), replace=False).tolist()))
+              for _ in range(int(rng.integers(5, 60)))]
+    lost = (rng.random(n) < rng.uniform(0.05, 0.5)).astype(np.uint8)
+    ptr, idx = _csr(groups)
+    path = oracle.local_path(ptr, idx, n, lost)
+    unknown = set(np.nonzero(lost)[0].tolist())
+    for pairs in path.levels():
+        cand = {}
+        for q, grp in enumerate(groups):
+            u = [s for s in grp if s in unknown]
+            if len(u) == 1:
+                cand.setdefault(u[0], []).append((len(grp), q))
+        assert {f for f, _ in pairs} == set(cand)
+        for f, q in pairs:
+            assert (len(groups[q]), q) == min(cand[f])
+        unknown -= {f for f, _ in pairs}
+    assert set(np.nonzero(path.unrepaired)[0].tolist()) == unknown
