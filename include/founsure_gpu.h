@@ -91,8 +91,8 @@ typedef struct fs_code fs_code; /* opaque; owned by the library */
  *            b + j (data blocks and earlier parities; its own parity b + j is
  *            implied), and the checks come in level order (level = 1 + the
  *            deepest parity member). Chained codes encode level by level with
- *            the row-gather kernels, and fs_update pushes deltas through the
- *            levels in order; batched encodes reject them.
+ *            the row-gather kernels (single calls and batches), and fs_update
+ *            pushes deltas through the levels in order.
  *   lt:      n rows (coded blocks) over n_cols = k_int = b + m intermediates.
  * With precode == NULL, b is taken as lt->n_cols. block_bytes = t.
  * Validates both graphs on the host (bounds, ascending rows, sizes; empty

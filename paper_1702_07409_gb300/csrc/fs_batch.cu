@@ -23,7 +23,6 @@ bool stripe_ok(const fs_stripe &s, int op, int device) {
     const fs_code *c = s.code;
     if (!c || c->device != device) return false;
     if (op == FS_OP_ENCODE) {
-        if (c->chained) return false;  // batched encodes take one precode launch
         if (!s.d_data || !s.d_coded) return false;
         if ((c->m > 0) != (s.d_parity != nullptr)) return false;
         return aligned16(s.d_data) && aligned16(s.d_parity) && aligned16(s.d_coded);

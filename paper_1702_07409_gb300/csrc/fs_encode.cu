@@ -1073,9 +1073,15 @@ cudaError_t launch_encode(const fs_code *c, const void *data, void *parity, void
 // every parity final before an LT row reads it). Tickets run stripe by stripe.
 
 struct EncodeBatch {
-    RowArgs *d_pre = nullptr, *d_lt = nullptr;  // device job arrays (row-gather stripes)
-    int n_pre = 0, n_lt = 0;
-    int32_t t_pre = 0, t_lt = 0;  // tickets of each launch
+    // device job arrays of the row-gather stripes: precode rows one launch per
+    // precode level (a chained precode's level reads earlier levels' parities),
+    // then the LT rows
+    std::vector<RowArgs *> d_pre;
+    std::vector<int> n_pre;
+    std::vector<int32_t> t_pre;  // tickets of each precode launch
+    RowArgs *d_lt = nullptr;
+    int n_lt = 0;
+    int32_t t_lt = 0;
     SliceArgs *d_sl = nullptr;    // slice stripes: arguments, tensor maps, items
     CUtensorMap *d_maps = nullptr;
     int4 *d_items = nullptr;
@@ -1093,8 +1099,10 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
                               void *const *parity, void *const *coded, int32_t n,
                               EncodeBatch **out) {
     *out = nullptr;
-    std::vector<RowArgs> pre, lt;
-    int64_t tp = 0, tl = 0;
+    std::vector<std::vector<RowArgs>> pre;  // per precode level
+    std::vector<int64_t> tp;
+    std::vector<RowArgs> lt;
+    int64_t tl = 0;
     // stripes whose slice layout fits (16-byte slots, two buffers) go to the
     // batch slice kernel; the layout of a launch is the largest buffers and
     // the largest tables of its stripes, so stripes are added while that fits
@@ -1146,19 +1154,26 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
         a.tw = c->tw;
         a.n_chunks = n_chunks;
         a.hints = 0;
-        if (c->m > 0) {
-            a.ptr = c->pre_ptr;
+        for (int32_t l = 0; c->m > 0 && l < c->n_pre_levels; ++l) {
+            const int32_t r0 = c->chained ? c->pre_level_off[l] : 0;
+            const int32_t r1 = c->chained ? c->pre_level_off[l + 1] : c->m;
+            if ((int32_t)pre.size() <= l) {
+                pre.emplace_back();
+                tp.push_back(0);
+            }
+            a.ptr = c->pre_ptr + r0;
             a.idx = c->pre_idx;
             a.inA = static_cast<const uint4 *>(data[i]);
-            a.inB = nullptr;
+            a.inB = c->chained ? static_cast<const uint4 *>(parity[i]) : nullptr;
             a.split = c->b;
-            a.out = static_cast<uint4 *>(parity[i]);
-            a.n_rows = c->m;
+            a.out = static_cast<uint4 *>(parity[i]) + (int64_t)r0 * c->tw;
+            a.n_rows = r1 - r0;
             a.stream_out = 0;
             a.rows = 1;
-            a.t0 = (int32_t)tp;
-            tp += (int64_t)n_chunks * c->m;
-            pre.push_back(a);
+            a.t0 = (int32_t)tp[l];
+            tp[l] += (int64_t)n_chunks * a.n_rows;
+            pre[l].push_back(a);
+            if (tp[l] >= INT32_MAX - 4096) return cudaErrorInvalidValue;
         }
         if (c->n > 0) {
             a.ptr = c->con_ptr;
@@ -1174,12 +1189,15 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
             tl += (int64_t)n_chunks * ((c->n + a.rows - 1) / a.rows);
             lt.push_back(a);
         }
-        if (tp >= INT32_MAX - 4096 || tl >= INT32_MAX - 4096) return cudaErrorInvalidValue;
+        if (tl >= INT32_MAX - 4096) return cudaErrorInvalidValue;
     }
     EncodeBatch *b = new EncodeBatch();
-    b->n_pre = (int)pre.size();
+    b->d_pre.assign(pre.size(), nullptr);
+    for (size_t l = 0; l < pre.size(); ++l) {
+        b->n_pre.push_back((int)pre[l].size());
+        b->t_pre.push_back((int32_t)tp[l]);
+    }
     b->n_lt = (int)lt.size();
-    b->t_pre = (int32_t)tp;
     b->t_lt = (int32_t)tl;
     b->num_sms = n > 0 ? codes[0]->num_sms : 1;
     b->ctas = n > 0 ? std::min(codes[0]->gather_ctas, kCtasPerSm) : 1;
@@ -1187,7 +1205,8 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
     b->n_items = (int)items.size();
     b->smem_sl = smem_sl;
     cudaError_t e = plan_upload(&b->d_ctr, zero, 4);
-    if (e == cudaSuccess) e = plan_upload(&b->d_pre, pre.data(), pre.size());
+    for (size_t l = 0; l < pre.size() && e == cudaSuccess; ++l)
+        e = plan_upload(&b->d_pre[l], pre[l].data(), pre[l].size());
     if (e == cudaSuccess) e = plan_upload(&b->d_lt, lt.data(), lt.size());
     if (e == cudaSuccess) e = plan_upload(&b->d_sl, sl.data(), sl.size());
     if (e == cudaSuccess) e = plan_upload(&b->d_maps, maps.data(), maps.size());
@@ -1211,9 +1230,12 @@ cudaError_t encode_batch_run(const EncodeBatch *b, cudaStream_t s) {
                                                            b->d_ctr + 2, b->d_ctr + 3);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && b->t_pre > 0) {
-        k_rows_batch<<<grid_for(b->t_pre, b->num_sms, b->ctas), kEncThreads, 0, s>>>(
-            b->d_pre, b->n_pre, b->t_pre, b->d_ctr);
+    for (size_t l = 0; l < b->d_pre.size() && e == cudaSuccess; ++l) {
+        if (b->t_pre[l] <= 0) continue;
+        if (l > 0) e = cudaMemsetAsync(b->d_ctr, 0, sizeof(int32_t), s);  // fresh tickets
+        if (e != cudaSuccess) break;
+        k_rows_batch<<<grid_for(b->t_pre[l], b->num_sms, b->ctas), kEncThreads, 0, s>>>(
+            b->d_pre[l], b->n_pre[l], b->t_pre[l], b->d_ctr);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && b->t_lt > 0) {
@@ -1226,7 +1248,7 @@ cudaError_t encode_batch_run(const EncodeBatch *b, cudaStream_t s) {
 
 void encode_batch_free(EncodeBatch *b) {
     if (!b) return;
-    plan_free(b->d_pre);
+    for (RowArgs *p : b->d_pre) plan_free(p);
     plan_free(b->d_lt);
     plan_free(b->d_sl);
     plan_free(b->d_maps);

@@ -447,8 +447,8 @@ def test_array_precode_encode_decode(t):
     """The array LDPC precode of Algorithm 2 (b = 4154, k = 4288: p = 67, two
     levels of 67 checks, the second reading parities of the first) under an
     LT code of n = 5574: the level-by-level encode and the joint decode are
-    bit-exact against the oracle, and so is a delta update (parity levels in
-    order); batched encodes reject the chained code."""
+    bit-exact against the oracle, and so are a delta update and a batched
+    encode (parity levels in order)."""
     import torch
     fs = _fs()
     b, k, n = 4154, 4288, 5574
@@ -485,8 +485,35 @@ def test_array_precode_encode_decode(t):
     d.copy_(_dev(data))
     p.copy_(_dev(par))
     cd.copy_(_dev(cod))
-    with pytest.raises(fs.FounsureError):
-        fs.Batch([{"code": code, "data": d, "parity": p, "coded": cd}], fs.OP_ENCODE)
+    # a batch encode of the chained code beside a data-only precoded one (one
+    # precode launch per level), eager and from a captured CUDA graph
+    g2 = gen.make_graph(300, 12, 400, gen.DIST_FINITE40, stripe=5)
+    data2 = gen.fill_bytes(gen.SEED_DATA + 6, 300 * t).reshape(300, t)
+    code2 = fs.Code(g2, t)
+    d2b, p2b = _dev(data2), torch.empty((12, t), dtype=torch.uint8, device="cuda")
+    cd2 = torch.empty((400, t), dtype=torch.uint8, device="cuda")
+    pb = torch.empty_like(p)
+    cdb = torch.empty_like(cd)
+    enc = fs.Batch([{"code": code, "data": d, "parity": pb, "coded": cdb},
+                    {"code": code2, "data": d2b, "parity": p2b, "coded": cd2}], fs.OP_ENCODE)
+    enc.run()
+    torch.cuda.synchronize()
+    par2, cod2b = oracle.encode(g2, data2, t)
+    assert np.array_equal(_host(pb), par) and np.array_equal(_host(cdb), cod)
+    assert np.array_equal(_host(p2b), par2) and np.array_equal(_host(cd2), cod2b)
+    pb.zero_()
+    cdb.zero_()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph):
+            enc.run(torch.cuda.current_stream())
+    torch.cuda.current_stream().wait_stream(side)
+    graph.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(_host(pb), par) and np.array_equal(_host(cdb), cod)
+    assert enc.status() == fs.FS_OK
     out = torch.empty((b, t), dtype=torch.uint8, device="cuda")
     dec = fs.Batch([{"code": code, "coded": cd, "erased": _dev(_erased(n, 0.15, gen.SEED_ERASE + 5)),
                      "data_out": out, "unrecovered": torch.empty(k, dtype=torch.uint8, device="cuda"),
