@@ -271,6 +271,9 @@ struct SliceArgs {
     uint4 *parity, *coded;
     int32_t m, n_grp, n_grp_p, n_grp_a, bpad, zbase, slots, box_rows, n_boxes, nbuf;
     int32_t write_parity;     // 1: this part writes the parities out (the first part)
+    int32_t n_xphase;         // chained precode: parity levels after the first, and the
+    int32_t xphase_end[kSliceXPhases];  // end group of each (they start at n_grp_a)
+    int32_t par_hi;           // end of those levels' groups (n_grp_a when there are none)
     int64_t tw;               // 16-byte words per block
     int32_t n_slices;         // byte slices of the stripe
     int32_t *ticket;          // workspace counter, zero at launch
@@ -386,7 +389,8 @@ __device__ __forceinline__ void row_group(const SliceArgs &a, const SliceTables 
     }
     const uint16_t row = tb.grow[q * 32 + lane];
     if (row == kNoSlot) return;
-    if (q < a.n_grp_p) {  // a piece of a parity row: XOR it into the parity's slot
+    const bool piece = q < a.n_grp_p || (q >= a.n_grp_a && q < a.par_hi);
+    if (piece) {  // a piece of a parity row: XOR it into the parity's slot
 #pragma unroll
         for (int h = 0; h < V; ++h) red_xor16(slot + unit_of<V>(a.bpad + row, h), acc[h]);
     } else {
@@ -433,7 +437,10 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
     __shared__ int32_t s_ok;
     __shared__ int s_ctr[2];  // work counters of the two phases
     const int32_t n_slices = a.n_slices;
-    const int n_one = a.n_grp_a, n_two = a.n_grp - a.n_grp_a;  // groups of the two phases
+    // groups of the two phases (a chained precode's further parity levels run
+    // as extra phases between them)
+    const int hi_p = a.par_hi;
+    const int n_one = a.n_grp_a, n_two = a.n_grp - hi_p;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i)
@@ -490,11 +497,18 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
         drain(&s_ctr[0], n_one, [&](int i) { row_group<V>(a, tb, slot, i, w0); });
         __syncthreads();  // the parity slots are complete
         if (threadIdx.x == 0) s_ctr[0] = 0;
+        for (int ph = 0; ph < a.n_xphase; ++ph) {  // chained: the next level reads these
+            const int lo = ph == 0 ? a.n_grp_a : a.xphase_end[ph - 1], hi = a.xphase_end[ph];
+            __syncthreads();  // the counter is reset
+            drain(&s_ctr[0], hi - lo, [&](int i) { row_group<V>(a, tb, slot, lo + i, w0); });
+            __syncthreads();  // this level's parity slots are complete
+            if (threadIdx.x == 0) s_ctr[0] = 0;
+        }
         for (int i = threadIdx.x; a.write_parity && i < a.m * V; i += blockDim.x) {
             const int j = i / V, h = i - j * V;
             if (w0 + h < a.tw) a.parity[(int64_t)j * a.tw + w0 + h] = slot[unit_of<V>(a.bpad + j, h)];
         }
-        drain(&s_ctr[1], n_two, [&](int i) { row_group<V>(a, tb, slot, a.n_grp_a + i, w0); });
+        drain(&s_ctr[1], n_two, [&](int i) { row_group<V>(a, tb, slot, hi_p + i, w0); });
         if (a.nbuf == 1) {
             __syncthreads();  // the only buffer is free
             zero_parities<V>(a, slot0);
@@ -686,9 +700,10 @@ std::vector<int> colour_edges(const std::vector<std::pair<int, int>> &edges, int
 cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t *con_idx) {
     c->sl_slots = 0;
     c->sl_parts = 0;
-    // a chained precode (parities over earlier parities) needs its levels in
-    // order: such codes take the row-gather encode
-    if (c->chained || c->b < 1 || c->n < 1 || c->n >= kNoSlot || c->m >= kNoSlot) return cudaSuccess;
+    // a chained precode (parities over earlier parities) runs its levels as
+    // phases of their own: at most 1 + kSliceXPhases levels
+    if (c->b < 1 || c->n < 1 || c->n >= kNoSlot || c->m >= kNoSlot) return cudaSuccess;
+    if (c->chained && c->n_pre_levels - 1 > kSliceXPhases) return cudaSuccess;
     const int32_t box_rows = c->b < 256 ? c->b : 256;
     const int64_t bpad = ((int64_t)c->b + box_rows - 1) / box_rows * box_rows;
     // data slots, parity slots, then 8 zero slots (one per bank group)
@@ -733,7 +748,13 @@ cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t
     struct HostPart {
         std::vector<unsigned char> tab;
         int32_t n_grp = 0, n_grp_p = 0, n_grp_a = 0, off_row = 0, off_idx = 0;
+        int32_t n_xphase = 0;
+        int32_t xphase_end[kSliceXPhases] = {};
     };
+    // precode level of parity j (0 unless chained: its checks come in level order)
+    std::vector<int32_t> plevel(m, 0);
+    for (int32_t l = 0; c->chained && l < c->n_pre_levels; ++l)
+        for (int32_t j = c->pre_level_off[l]; j < c->pre_level_off[l + 1]; ++j) plevel[j] = l;
     std::vector<char> used((size_t)mp + n, 0);
     auto make_part = [&](int32_t r_lo, int32_t r_hi, HostPart &hp) -> bool {
         std::vector<Quarter> quarters;
@@ -789,7 +810,11 @@ cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t
         // parity rows; coded rows that read no parity (computed beside the
         // parities); coded rows that read one (after them)
         std::vector<int32_t> set_p, set_a, set_b;
-        for (int32_t p = 0; p < mp; ++p) set_p.push_back(p);
+        std::vector<std::vector<int32_t>> set_x(c->chained ? c->n_pre_levels - 1 : 0);
+        for (int32_t p = 0; p < mp; ++p) {
+            const int32_t l = plevel[p / ks];
+            (l == 0 ? set_p : set_x[l - 1]).push_back(p);
+        }
         for (int32_t r = r_lo; r < r_hi; ++r) {
             bool par = false;
             for (int32_t e = con_ptr[r]; e < con_ptr[r + 1]; ++e) par |= con_idx[e] >= c->b;
@@ -799,6 +824,11 @@ cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t
         hp.n_grp_p = (int32_t)(quarters.size() / 4);
         build_quarters(set_a);
         hp.n_grp_a = (int32_t)(quarters.size() / 4);
+        hp.n_xphase = (int32_t)set_x.size();
+        for (size_t l = 0; l < set_x.size(); ++l) {  // one phase per further level
+            build_quarters(set_x[l]);
+            hp.xphase_end[l] = (int32_t)(quarters.size() / 4);
+        }
         build_quarters(set_b);
         const int32_t n_grp = (int32_t)(quarters.size() / 4);
         hp.n_grp = n_grp;
@@ -899,6 +929,8 @@ cudaError_t build_slice_tables(fs_code *c, const int32_t *con_ptr, const int32_t
         sp.n_grp_a = hp.n_grp_a;
         sp.off_row = hp.off_row;
         sp.off_idx = hp.off_idx;
+        sp.n_xphase = hp.n_xphase;
+        for (int l = 0; l < kSliceXPhases; ++l) sp.xphase_end[l] = hp.xphase_end[l];
     }
     c->sl_parts = (int32_t)parts.size();
     c->sl_box_rows = box_rows;
@@ -946,6 +978,9 @@ bool slice_setup(const fs_code *c, int part, const void *data, void *parity, voi
     a->n_grp = sp.n_grp;
     a->n_grp_p = sp.n_grp_p;
     a->n_grp_a = sp.n_grp_a;
+    a->n_xphase = sp.n_xphase;
+    for (int l = 0; l < kSliceXPhases; ++l) a->xphase_end[l] = sp.xphase_end[l];
+    a->par_hi = sp.n_xphase > 0 ? sp.xphase_end[sp.n_xphase - 1] : sp.n_grp_a;
     a->bpad = c->sl_bpad;
     a->zbase = c->sl_zbase;
     a->slots = c->sl_slots;
@@ -1116,7 +1151,8 @@ cudaError_t encode_batch_plan(const fs_code *const *codes, const void *const *da
     // (in a batch only single-part codes: beside many other stripes the
     // row-gather kernel overlaps the large ones better than a split would)
     for (int32_t i = 0; i < n; ++i)
-        if (codes[i]->encode_slices && slices_pay(codes[i]) && codes[i]->sl_parts == 1)
+        if (codes[i]->encode_slices && slices_pay(codes[i]) && codes[i]->sl_parts == 1 &&
+            !codes[i]->chained)  // the batch slice kernel runs two phases only
             order.push_back(i);
     std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return tab_of(x) < tab_of(y); });
     // every stripe lays out its own tables and two buffers, so a stripe

@@ -22,11 +22,16 @@
 // The first n_grp_p groups are precode (parity) rows, groups up to n_grp_a
 // coded rows that read no parity, the rest coded rows that read one.
 constexpr int kSliceParts = 4;
+constexpr int kSliceXPhases = 7;  // further precode levels a slice encode takes (chained)
 struct SlicePart {
     unsigned char *tab = nullptr;
     int32_t tab_bytes = 0;  // multiple of 16
     int32_t n_grp = 0, n_grp_p = 0, n_grp_a = 0;
     int32_t off_row = 0, off_idx = 0;  // byte offsets
+    // chained precode: the parity pieces of levels 1, 2, ... are the groups
+    // [n_grp_a, xphase_end[0]), [xphase_end[0], xphase_end[1]), ...
+    int32_t n_xphase = 0;
+    int32_t xphase_end[kSliceXPhases] = {};
 };
 
 struct fs_code {
