@@ -411,7 +411,7 @@ def run_gpu(args):
                    "reasons": clocks["reasons"]},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_slice)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_slice, args.cpu_steps)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -1064,6 +1064,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-slice", type=int, default=16384,
                     help="bytes of each block the CPU oracle processes per step")
+    ap.add_argument("--cpu-steps", type=int, default=12,
+                    help="steps of the oracle in cpu_baseline (about 0.85 s each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l2-hints", action="store_true",
                     help="tuning knob: L2 evict-last / evict-first hints")
