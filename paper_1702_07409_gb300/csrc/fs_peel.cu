@@ -41,7 +41,8 @@
 //   each 16-byte chunk), plus an L2 prefetch of level l+1's coded payloads. A recipe is gathered in segments of kRecipeSeg
 //   entries, one thread per (segment, word pair), all loads of a segment in
 //   flight at once; pairs with several segments combine them in
-//   shared-memory accumulators before the block is written.
+//   shared-memory accumulators, and the segment whose count completes a
+//   word pair's sum writes it out (no second barrier in the level).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -805,9 +806,14 @@ __device__ __forceinline__ void peel_body(const PeelArgs &a, int64_t slice) {
         int32_t *chunks = segs + 3 * kStageSegs;                       // [3][R / 4]
         int32_t *rows = chunks + 3 * (kStageRecipe / 4);               // [2][R]
         uint4 *accs = reinterpret_cast<uint4 *>(rows + 2 * kStageRecipe);  // [kStageMulti][L]
+        // segments of each (multi-segment pair, word pair) summed so far: the
+        // segment that completes a sum writes it out
+        int32_t *done = reinterpret_cast<int32_t *>(accs + (size_t)kStageMulti * L);
+        const int nvl = (L + kPeelV - 1) / kPeelV;  // [kStageMulti][nvl]
         for (int i = threadIdx.x; i < 2 * (nl + 1); i += blockDim.x) ltab[i] = a.level_tab[i];
         for (int i = threadIdx.x; i < kStageMulti * L; i += blockDim.x)
             accs[i] = make_uint4(0, 0, 0, 0);
+        for (int i = threadIdx.x; i < kStageMulti * nvl; i += blockDim.x) done[i] = 0;
         if (threadIdx.x == 0) {
             for (int k = 0; k < 3; ++k) mbar_init(&mb_pairs[k]);
             asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -851,8 +857,7 @@ __device__ __forceinline__ void peel_body(const PeelArgs &a, int64_t slice) {
                            chunks + ((l + 1) % 3) * (kStageRecipe / 4),
                            rows + ((l + 1) & 1) * kStageRecipe, w0, lanes);
             cp_async_commit();
-            const int4 lt = ltab[2 * l];
-            const int np = lt.y, ns = lt.w;
+            const int ns = ltab[2 * l].w;
             const uint64_t pol_last = l2_policy_last(), pol_first = l2_policy_first();
             // every (segment, word pair): one gather of at most kRecipeSeg blocks;
             // items go to the highest threads first, so the staging above (thread
@@ -899,19 +904,21 @@ __device__ __forceinline__ void peel_body(const PeelArgs &a, int64_t slice) {
                         if (two) dst[1] = acc1;
                     }
                 } else {  // one of several segments: combine in shared memory
-                    xor_shared(accs + slot * L + k * kPeelV, acc0);
-                    if (two) xor_shared(accs + slot * L + k * kPeelV + 1, acc1);
-                }
-            }
-            if (ns > np) {  // some pair has several segments: write their sums
-                __syncthreads();
-                for (int it = rt; it < np * lanes; it += blockDim.x) {
-                    const int q = it / lanes, lane = it - q * lanes;
-                    const int32_t *rec = pc + (size_t)q * kRec;
-                    const int slot = rec[3];
-                    if (slot < 0) continue;
-                    block_ptr(a, rec[0])[w0 + lane] = accs[slot * L + lane];
-                    accs[slot * L + lane] = make_uint4(0, 0, 0, 0);
+                    uint4 *sa = accs + slot * L + k * kPeelV;
+                    xor_shared(sa, acc0);
+                    if (two) xor_shared(sa + 1, acc1);
+                    __threadfence_block();  // the sum holds this segment before it counts
+                    if (atomicAdd(&done[slot * nvl + k], 1) == rec[7] - 1) {
+                        // the last segment of this word pair: every other one is in
+                        __threadfence_block();
+                        const uint4 v0 = sa[0], v1 = two ? sa[1] : v0;
+                        uint4 *dst = block_ptr(a, f) + w;
+                        dst[0] = v0;
+                        if (two) dst[1] = v1;
+                        sa[0] = make_uint4(0, 0, 0, 0);
+                        if (two) sa[1] = make_uint4(0, 0, 0, 0);
+                        done[slot * nvl + k] = 0;  // the slot is free for a later level
+                    }
                 }
             }
         }
@@ -940,7 +947,7 @@ size_t peel_smem_bytes(int64_t L) {
     return (size_t)(kStageLevels + 1) * 32 + (size_t)3 * kStagePairs * kRec * 4 +
            (size_t)3 * kStageSegs * 4 + (size_t)3 * (kStageRecipe / 4) * 4 +
            (size_t)2 * kStageRecipe * 4 +
-           (size_t)kStageMulti * L * 16;
+           (size_t)kStageMulti * L * 16 + (size_t)kStageMulti * ((L + kPeelV - 1) / kPeelV) * 4;
 }
 
 }  // namespace
