@@ -45,7 +45,7 @@ METRIC = "encode & BP-decode source GB/s"
 # captures summarised in profiles/k_peel_precoded_k4096_t64k.md and
 # profiles/k_slices_precoded_k4096_t64k.md (valid while those kernels are
 # unchanged)
-PEEL_TRAFFIC_BYTES = 1037988096 + 278271232
+PEEL_TRAFFIC_BYTES = 1039106048 + 278187008
 SLICES_TRAFFIC_BYTES = 273448192 + 313286656
 WORKLOAD = ("precoded LDGM stripe: b=4096 x 64 KiB data, m=128 checks (3 per data block), "
             "n=5400, FiniteDist max-degree-40, 20% erasures; step = encode + decode + "

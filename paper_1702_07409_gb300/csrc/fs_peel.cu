@@ -39,10 +39,11 @@
 //   aligned), the padded graph rows (recipes) of level l+1 with 16-byte
 //   cp.async copies spread over all threads (a chunk list names the pair of
 //   each 16-byte chunk), plus an L2 prefetch of level l+1's coded payloads. A recipe is gathered in segments of kRecipeSeg
-//   entries, one thread per (segment, word pair), all loads of a segment in
+//   entries, one thread per (segment, word), all loads of a segment in
 //   flight at once; pairs with several segments combine them in
 //   shared-memory accumulators, and the segment whose count completes a
-//   word pair's sum writes it out (no second barrier in the level).
+//   word's sum writes it out (no second barrier in the level). 1024 threads
+//   of at most 64 registers: twice the warps of 2-word items, which need more.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -55,8 +56,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kDpgThreads = 1024;  // fills an SM's registers: no other kernel's CTA shares it
-constexpr int kPeelThreads = 512;
-constexpr int kPeelV = 2;           // 16-byte words per payload item
+constexpr int kPeelThreads = 1024;  // 64 registers a thread: one item (segment, word) each
 constexpr int kPeelLmax = 64;       // largest slice (words) of one payload CTA
 constexpr int kStagePairs = 256;    // pairs of one level held in shared memory
 constexpr int kStageRecipe = 4096;  // recipe entries of one level held in shared memory
@@ -794,7 +794,6 @@ __device__ __forceinline__ void peel_body(const PeelArgs &a, int64_t slice) {
     const int L = a.L;
     const int64_t w0 = slice * L;
     const int lanes = (int)min((int64_t)L, a.tw - w0);
-    const int nv = (lanes + kPeelV - 1) / kPeelV;  // word pairs of this slice
     const int32_t nl = a.hdr[WS_N_LEVELS];
 
     if (!a.hdr[WS_STAGED]) {
@@ -806,14 +805,13 @@ __device__ __forceinline__ void peel_body(const PeelArgs &a, int64_t slice) {
         int32_t *chunks = segs + 3 * kStageSegs;                       // [3][R / 4]
         int32_t *rows = chunks + 3 * (kStageRecipe / 4);               // [2][R]
         uint4 *accs = reinterpret_cast<uint4 *>(rows + 2 * kStageRecipe);  // [kStageMulti][L]
-        // segments of each (multi-segment pair, word pair) summed so far: the
+        // segments of each (multi-segment pair, word) summed so far: the
         // segment that completes a sum writes it out
-        int32_t *done = reinterpret_cast<int32_t *>(accs + (size_t)kStageMulti * L);
-        const int nvl = (L + kPeelV - 1) / kPeelV;  // [kStageMulti][nvl]
+        int32_t *done = reinterpret_cast<int32_t *>(accs + (size_t)kStageMulti * L);  // [kStageMulti][L]
         for (int i = threadIdx.x; i < 2 * (nl + 1); i += blockDim.x) ltab[i] = a.level_tab[i];
         for (int i = threadIdx.x; i < kStageMulti * L; i += blockDim.x)
             accs[i] = make_uint4(0, 0, 0, 0);
-        for (int i = threadIdx.x; i < kStageMulti * nvl; i += blockDim.x) done[i] = 0;
+        for (int i = threadIdx.x; i < kStageMulti * L; i += blockDim.x) done[i] = 0;
         if (threadIdx.x == 0) {
             for (int k = 0; k < 3; ++k) mbar_init(&mb_pairs[k]);
             asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -859,65 +857,49 @@ __device__ __forceinline__ void peel_body(const PeelArgs &a, int64_t slice) {
             cp_async_commit();
             const int ns = ltab[2 * l].w;
             const uint64_t pol_last = l2_policy_last(), pol_first = l2_policy_first();
-            // every (segment, word pair): one gather of at most kRecipeSeg blocks;
+            // every (segment, word): one gather of at most kRecipeSeg blocks;
             // items go to the highest threads first, so the staging above (thread
             // 0's bulk copies, the low threads' row copies) overlaps them
             const int rt = (int)blockDim.x - 1 - (int)threadIdx.x;
-            for (int it = rt; it < ns * nv; it += blockDim.x) {
-                const int s = it / nv, k = it - s * nv;
+            for (int it = rt; it < ns * lanes; it += blockDim.x) {
+                const int s = it / lanes, k = it - s * lanes;
                 const int32_t *rec = pc + (size_t)sp[s] * kRec;
                 const int32_t f = rec[0], g = rec[1], slot = rec[3];
                 const int sidx = s - rec[6];
                 const int32_t rs = rec[2] + sidx * kRecipeSeg;
                 const int32_t cnt = min(kRecipeSeg, rec[2] + rec[5] - rs);
-                const int64_t w = w0 + k * kPeelV;
-                const bool two = k * kPeelV + 1 < lanes;
-                uint4 acc0 = make_uint4(0, 0, 0, 0), acc1 = acc0;
+                const int64_t w = w0 + k;
+                uint4 acc = make_uint4(0, 0, 0, 0);
                 if (sidx == 0 && g < a.n) {
                     const uint4 *src = a.coded + (int64_t)g * a.tw + w;
-                    acc0 = a.hints ? ld_nc_hint(src, pol_first) : src[0];
-                    if (two) acc1 = a.hints ? ld_nc_hint(src + 1, pol_first) : src[1];
+                    acc = a.hints ? ld_nc_hint(src, pol_first) : src[0];
                 }
-                uint4 x0[kRecipeSeg], x1[kRecipeSeg];
+                uint4 x[kRecipeSeg];  // every load of the segment in flight at once
 #pragma unroll
                 for (int j = 0; j < kRecipeSeg; ++j) {
                     const int32_t h = j < cnt ? hs[rs + j] : -1;
-                    x0[j] = x1[j] = make_uint4(0, 0, 0, 0);
+                    x[j] = make_uint4(0, 0, 0, 0);
                     if (h >= 0 && h != f) {
                         const uint4 *src = block_ptr(a, h) + w;
-                        x0[j] = a.hints ? ld_hint(src, pol_last) : src[0];
-                        if (two) x1[j] = a.hints ? ld_hint(src + 1, pol_last) : src[1];
+                        x[j] = a.hints ? ld_hint(src, pol_last) : src[0];
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < kRecipeSeg; ++j) {
-                    xor4(acc0, x0[j]);
-                    xor4(acc1, x1[j]);
-                }
+                for (int j = 0; j < kRecipeSeg; ++j) xor4(acc, x[j]);
                 if (slot < 0) {
                     uint4 *dst = block_ptr(a, f) + w;
-                    if (a.hints) {
-                        st_hint(dst, acc0, pol_last);
-                        if (two) st_hint(dst + 1, acc1, pol_last);
-                    } else {
-                        dst[0] = acc0;
-                        if (two) dst[1] = acc1;
-                    }
+                    if (a.hints) st_hint(dst, acc, pol_last);
+                    else dst[0] = acc;
                 } else {  // one of several segments: combine in shared memory
-                    uint4 *sa = accs + slot * L + k * kPeelV;
-                    xor_shared(sa, acc0);
-                    if (two) xor_shared(sa + 1, acc1);
+                    uint4 *sa = accs + slot * L + k;
+                    xor_shared(sa, acc);
                     __threadfence_block();  // the sum holds this segment before it counts
-                    if (atomicAdd(&done[slot * nvl + k], 1) == rec[7] - 1) {
-                        // the last segment of this word pair: every other one is in
+                    if (atomicAdd(&done[slot * L + k], 1) == rec[7] - 1) {
+                        // the last segment of this word: every other one is in
                         __threadfence_block();
-                        const uint4 v0 = sa[0], v1 = two ? sa[1] : v0;
-                        uint4 *dst = block_ptr(a, f) + w;
-                        dst[0] = v0;
-                        if (two) dst[1] = v1;
+                        block_ptr(a, f)[w] = sa[0];
                         sa[0] = make_uint4(0, 0, 0, 0);
-                        if (two) sa[1] = make_uint4(0, 0, 0, 0);
-                        done[slot * nvl + k] = 0;  // the slot is free for a later level
+                        done[slot * L + k] = 0;  // the slot is free for a later level
                     }
                 }
             }
@@ -947,7 +929,7 @@ size_t peel_smem_bytes(int64_t L) {
     return (size_t)(kStageLevels + 1) * 32 + (size_t)3 * kStagePairs * kRec * 4 +
            (size_t)3 * kStageSegs * 4 + (size_t)3 * (kStageRecipe / 4) * 4 +
            (size_t)2 * kStageRecipe * 4 +
-           (size_t)kStageMulti * L * 16 + (size_t)kStageMulti * ((L + kPeelV - 1) / kPeelV) * 4;
+           (size_t)kStageMulti * L * 16 + (size_t)kStageMulti * L * 4;
 }
 
 }  // namespace
@@ -1030,14 +1012,13 @@ cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws, uin
 
 namespace {
 
-// slice width: every slice in flight at once (peel_ctas CTAs per SM), a whole
-// number of word pairs, at most kPeelLmax words
+// slice width: every slice in flight at once (peel_ctas CTAs per SM), at
+// most kPeelLmax words
 int64_t peel_slice_words(const fs_code *c) {
     const int64_t ctas = (int64_t)c->num_sms * c->peel_ctas;
     int64_t Lw = (c->tw + ctas - 1) / ctas;
-    Lw = (Lw + kPeelV - 1) / kPeelV * kPeelV;
     if (Lw > kPeelLmax) Lw = kPeelLmax;
-    if (Lw < kPeelV) Lw = kPeelV;
+    if (Lw < 1) Lw = 1;
     return Lw;
 }
 
@@ -1074,8 +1055,9 @@ cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, u
     cudaError_t e =
         cudaFuncSetAttribute(k_peel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // one CTA per SM: 512 threads; several: the SM's threads split between them
-    const int threads = c->peel_ctas >= 4 ? 128 : (c->peel_ctas >= 2 ? 256 : kPeelThreads);
+    // one CTA per SM: 1024 threads; several: the SM's threads split between them
+    const int threads =
+        c->peel_ctas >= 4 ? kPeelThreads / 4 : (c->peel_ctas >= 2 ? kPeelThreads / 2 : kPeelThreads);
     const int64_t n_slices = (c->tw + Lw - 1) / Lw;
     k_peel<<<(unsigned)n_slices, threads, smem, s>>>(a);
     return cudaGetLastError();
