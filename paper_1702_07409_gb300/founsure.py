@@ -142,6 +142,12 @@ def _check(rc: int, what: str) -> None:
         raise FounsureError(rc, what)
 
 
+def _call(name: str, *args) -> int:
+    """Calls a library function with arguments already marshalled (so a bad
+    argument is refused before the library is loaded)."""
+    return getattr(lib(), name)(*args)
+
+
 def _addr(x) -> Optional[int]:
     """Device address of a CUDA tensor (or an int address, or None)."""
     if x is None:
@@ -203,12 +209,6 @@ class Code:
         self._h = h
         self._lib = lib()
 
-    def status(self) -> int:
-        """Device status of the last run (blocking)."""
-        st = ctypes.c_int32(0)
-        _check(lib().fs_batch_status(self._h, ctypes.byref(st)), "fs_batch_status")
-        return int(st.value)
-
     def close(self) -> None:
         if getattr(self, "_h", None):
             self._lib.fs_code_destroy(self._h)
@@ -249,8 +249,9 @@ class Code:
         self._need(data, self.b * self.t, "data")
         self._need(parity, self.m * self.t, "parity")
         self._need(coded, self.n * self.t, "coded")
-        _check(lib().fs_encode(self._h, _addr(data), _addr(parity), _addr(coded), _addr(ws),
-                               _stream(stream)), "fs_encode")
+        self._need(ws, self.workspace_bytes(OP_ENCODE), "ws")
+        _check(_call("fs_encode", self._h, _addr(data), _addr(parity), _addr(coded), _addr(ws),
+                     _stream(stream)), "fs_encode")
 
     def encode_static(self, data, parity, coded, status=None, stream=None) -> None:
         """fs_encode_static: the encode with the library's static scratch area
@@ -258,33 +259,43 @@ class Code:
         self._need(data, self.b * self.t, "data")
         self._need(parity, self.m * self.t, "parity")
         self._need(coded, self.n * self.t, "coded")
-        _check(lib().fs_encode_static(self._h, _addr(data), _addr(parity), _addr(coded),
-                                      _addr(status), _stream(stream)), "fs_encode_static")
+        _check(_call("fs_encode_static", self._h, _addr(data), _addr(parity), _addr(coded),
+                     _addr(status), _stream(stream)), "fs_encode_static")
 
     def encode_rows(self, row_begin, row_end, data, parity, coded, ws, stream=None) -> None:
-        _check(lib().fs_encode_rows(self._h, row_begin, row_end, _addr(data), _addr(parity),
-                                    _addr(coded), _addr(ws), _stream(stream)), "fs_encode_rows")
+        self._need(data, self.b * self.t, "data")
+        self._need(parity, self.m * self.t, "parity")
+        self._need(coded, self.n * self.t, "coded")
+        self._need(ws, self.workspace_bytes(OP_ENCODE), "ws")
+        _check(_call("fs_encode_rows", self._h, row_begin, row_end, _addr(data), _addr(parity),
+                     _addr(coded), _addr(ws), _stream(stream)), "fs_encode_rows")
 
     def decode(self, coded, erased, data_out, unrecovered, n_unrecovered, ws, stream=None) -> None:
         self._need(coded, self.n * self.t, "coded")
         self._need(erased, self.n, "erased")
         self._need(data_out, self.b * self.t, "data_out")
         self._need(unrecovered, self.k_int, "unrecovered")
+        self._need(n_unrecovered, 4, "n_unrecovered")
         self._need(ws, self.workspace_bytes(OP_DECODE), "ws")
-        _check(lib().fs_decode(self._h, _addr(coded), _addr(erased), _addr(data_out),
-                               _addr(unrecovered), _addr(n_unrecovered), _addr(ws),
-                               _stream(stream)), "fs_decode")
+        _check(_call("fs_decode", self._h, _addr(coded), _addr(erased), _addr(data_out),
+                     _addr(unrecovered), _addr(n_unrecovered), _addr(ws),
+                     _stream(stream)), "fs_decode")
 
     def decode_schedule(self, erased, unrecovered, n_unrecovered, ws, stream=None) -> None:
+        self._need(erased, self.n, "erased")
+        self._need(unrecovered, self.k_int, "unrecovered")
+        self._need(n_unrecovered, 4, "n_unrecovered")
         self._need(ws, self.workspace_bytes(OP_DECODE), "ws")
-        _check(lib().fs_decode_schedule(self._h, _addr(erased), _addr(unrecovered),
-                                        _addr(n_unrecovered), _addr(ws), _stream(stream)),
+        _check(_call("fs_decode_schedule", self._h, _addr(erased), _addr(unrecovered),
+                     _addr(n_unrecovered), _addr(ws), _stream(stream)),
                "fs_decode_schedule")
 
     def decode_payload(self, coded, data_out, ws, stream=None) -> None:
+        self._need(coded, self.n * self.t, "coded")
         self._need(data_out, self.b * self.t, "data_out")
-        _check(lib().fs_decode_payload(self._h, _addr(coded), _addr(data_out), _addr(ws),
-                                       _stream(stream)), "fs_decode_payload")
+        self._need(ws, self.workspace_bytes(OP_DECODE), "ws")
+        _check(_call("fs_decode_payload", self._h, _addr(coded), _addr(data_out), _addr(ws),
+                     _stream(stream)), "fs_decode_payload")
 
     def decode_path(self, ws):
         """Views into a decode workspace after fs_decode (synchronises):
@@ -309,14 +320,23 @@ class Code:
                     parity=at(v.parity, self.m * self.t, torch.uint8))
 
     def update(self, idx, n_idx: int, new, data, parity, coded, ws, stream=None) -> None:
+        self._need(idx, 4 * n_idx, "idx")
         self._need(new, n_idx * self.t, "new")
+        self._need(data, self.b * self.t, "data")
+        self._need(parity, self.m * self.t, "parity")
+        self._need(coded, self.n * self.t, "coded")
         self._need(ws, self.workspace_bytes(OP_UPDATE, n_idx), "ws")
-        _check(lib().fs_update(self._h, _addr(idx), n_idx, _addr(new), _addr(data), _addr(parity),
-                               _addr(coded), _addr(ws), _stream(stream)), "fs_update")
+        _check(_call("fs_update", self._h, _addr(idx), n_idx, _addr(new), _addr(data),
+                     _addr(parity), _addr(coded), _addr(ws), _stream(stream)), "fs_update")
 
     def repair(self, lost, n_lost: int, data, parity, coded, ws, stream=None) -> None:
-        _check(lib().fs_repair(self._h, _addr(lost), n_lost, _addr(data), _addr(parity),
-                               _addr(coded), _addr(ws), _stream(stream)), "fs_repair")
+        self._need(lost, 4 * n_lost, "lost")
+        self._need(data, self.b * self.t, "data")
+        self._need(parity, self.m * self.t, "parity")
+        self._need(coded, self.n * self.t, "coded")
+        self._need(ws, self.workspace_bytes(OP_REPAIR, n_lost), "ws")
+        _check(_call("fs_repair", self._h, _addr(lost), n_lost, _addr(data), _addr(parity),
+                     _addr(coded), _addr(ws), _stream(stream)), "fs_repair")
 
 
 class Batch:
