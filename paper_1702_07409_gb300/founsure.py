@@ -356,13 +356,15 @@ class Batch:
             if op == OP_ENCODE:
                 code._need(s["data"], code.b * code.t, "data")
                 code._need(s.get("parity"), code.m * code.t, "parity")
-                code._need(s["coded"], code.n * code.t, "coded")
-            elif op == OP_DECODE:  # other ops are left to the library to reject
-                code._need(s["coded"], code.n * code.t, "coded")
-                code._need(s["data_out"], code.b * code.t, "data_out")
-                code._need(s["ws"], code.workspace_bytes(OP_DECODE), "ws")
-            elif op == OP_SCHEDULE:
-                code._need(s["ws"], code.workspace_bytes(OP_DECODE), "ws")
+                code._need(s.get("coded"), code.n * code.t, "coded")
+            elif op in (OP_DECODE, OP_SCHEDULE):  # other ops: the library rejects them
+                if op == OP_DECODE:
+                    code._need(s.get("coded"), code.n * code.t, "coded")
+                    code._need(s.get("data_out"), code.b * code.t, "data_out")
+                code._need(s.get("erased"), code.n, "erased")
+                code._need(s.get("unrecovered"), code.k_int, "unrecovered")
+                code._need(s.get("n_unrecovered"), 4, "n_unrecovered")
+                code._need(s.get("ws"), code.workspace_bytes(OP_DECODE), "ws")
             arr[i] = _Stripe(code._h, _addr(s.get("data")), _addr(s.get("parity")),
                              _addr(s.get("coded")), _addr(s.get("erased")),
                              _addr(s.get("data_out")), _addr(s.get("unrecovered")),
@@ -473,6 +475,12 @@ class Local:
     def repair(self, lost, coded, block_bytes: int, unrepaired, n_unrepaired, ws,
                stream=None) -> None:
         """Repairs the lost coded blocks of ``coded`` in place (fs_repair_local)."""
+        need = ((lost, self.n, "lost"), (coded, self.n * int(block_bytes), "coded"),
+                (unrepaired, self.n, "unrepaired"), (n_unrepaired, 4, "n_unrepaired"),
+                (ws, int(self._lib.fs_local_workspace_bytes(self._h)), "ws"))
+        for x, nbytes, name in need:
+            if x is not None and not isinstance(x, int) and _nbytes(x) < nbytes:
+                raise ValueError("%s holds %d bytes, needs %d" % (name, _nbytes(x), nbytes))
         _check(self._lib.fs_repair_local(self._h, _addr(lost), _addr(coded), int(block_bytes),
                                          _addr(unrepaired), _addr(n_unrepaired), _addr(ws),
                                          _stream(stream)), "fs_repair_local")

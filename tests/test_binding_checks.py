@@ -73,3 +73,22 @@ def test_host_tensors_are_refused(op):
     method, spec = CALLS[op]
     with pytest.raises(ValueError, match="expected a CUDA tensor"):
         getattr(_code(), method)(*_args(spec))
+
+
+BATCH = {
+    fs.OP_DECODE: [("coded", N * T), ("erased", N), ("data_out", B * T), ("unrecovered", B + M),
+                   ("n_unrecovered", 4), ("ws", WS[fs.OP_DECODE])],
+    fs.OP_SCHEDULE: [("erased", N), ("unrecovered", B + M), ("n_unrecovered", 4),
+                     ("ws", WS[fs.OP_DECODE])],
+}
+
+
+@pytest.mark.parametrize("op", sorted(BATCH))
+def test_batch_stripes_are_checked(op):
+    """A batch refuses a stripe with a short buffer before it is created."""
+    spec = BATCH[op]
+    for short, _ in spec:
+        stripe = {"code": _code()}
+        stripe.update({name: _buf(size - 1 if name == short else size) for name, size in spec})
+        with pytest.raises(ValueError, match=r"^%s holds" % short):
+            fs.Batch([stripe], op)
