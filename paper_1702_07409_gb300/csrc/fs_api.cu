@@ -325,7 +325,7 @@ FS_API fs_status fs_encode_rows(const fs_code *c, int32_t row_begin, int32_t row
     if (!aligned16(d_data) || !aligned16(d_parity) || !aligned16(d_coded) || !aligned16(d_ws))
         return FS_ERR_INVALID;
     cudaStream_t s = as_stream(stream);
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(d_ws, 0, sizeof(int32_t), s);  // the status word
     GatherArgs a = lt_args(c, d_data, d_parity, d_coded, d_ws);
     a.row_base = row_begin;
     a.n_rows = row_end - row_begin;

@@ -159,10 +159,12 @@ def test_encode_rows_and_empty_calls():
     _, cod = oracle.encode(case.g, case.data, case.t)
     cd2 = torch.zeros_like(cd)
     ws = case.code.workspace(_fs().OP_ENCODE)
+    ws[:4].view(torch.int32).fill_(_fs().FS_ERR_INVALID)  # a stale status from an earlier call
     case.code.encode_rows(100, 250, d, p, cd2, ws)
     torch.cuda.synchronize()
     got = _host(cd2)
     assert np.array_equal(got[100:250], cod[100:250]) and not got[:100].any() and not got[250:].any()
+    assert _fs().Code.ws_status(ws) == _fs().FS_OK
     # n_idx = 0 and n_lost = 0 leave everything untouched
     before = (_host(d).copy(), _host(p).copy(), _host(cd).copy())
     case.code.update(None, 0, None, d, p, cd, case.code.workspace(_fs().OP_UPDATE, 0))
