@@ -71,7 +71,7 @@ def lib() -> ctypes.CDLL:
         L.or_dpg.restype = i32
         L.or_peel.argtypes = [i32, i32, i32, vp, vp, vp, vp, i64, vp, i32, vp, vp, vp, vp]
         L.or_peel.restype = ctypes.c_int
-        L.or_peel_immediate.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.or_peel_immediate.argtypes = [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.or_peel_immediate.restype = i32
         L.or_cga.argtypes = [i32, i32, vp, vp, i32, ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)),
                              ctypes.POINTER(ctypes.c_int64)]
@@ -189,15 +189,21 @@ def decode(g, coded: np.ndarray, erased: np.ndarray, t: int, mode: int = MODE_JO
     return peel(g, coded, path, t), path
 
 
-def peel_immediate(g, erased: np.ndarray, order: np.ndarray) -> np.ndarray:
+def peel_immediate(g, erased: np.ndarray, order: np.ndarray, with_sweeps: bool = False):
     """Algorithm 1 with immediate updates over constraints visited in
-    ``order`` (a permutation of 0..n+m-1). Returns the unrecovered flags."""
+    ``order`` (a permutation of 0..n+m-1). Returns the unrecovered flags, and
+    with ``with_sweeps`` also the number of sweeps that decoded something
+    (the iteration count t_m of Section 3.1)."""
     G = _G(g)
     k_int = G.b + G.m
     unrec = np.zeros(max(k_int, 1), np.uint8)
     order = _i32(order)
     assert order.size == G.n + G.m
-    lib().or_peel_immediate(*G.args(), _p(_u8(erased)) if G.n else None, _p(order), _p(unrec))
+    sw = ctypes.c_int32(0)
+    lib().or_peel_immediate(*G.args(), _p(_u8(erased)) if G.n else None, _p(order), _p(unrec),
+                            ctypes.byref(sw))
+    if with_sweeps:
+        return unrec[:k_int].copy(), int(sw.value)
     return unrec[:k_int].copy()
 
 

@@ -240,14 +240,17 @@ int or_peel(int32_t b, int32_t m, int32_t n,
  * 0..n+m-1), decode whenever a constraint has exactly one unknown, repeat
  * sweeps until one changes nothing. Writes unrecovered[v] like or_dpg and
  * returns the number of recovered intermediates. Symbolic only.
+ * *n_sweeps (may be NULL) receives the number of sweeps that decoded at
+ * least one symbol: the iteration count t_m of Section 3.1, to set beside
+ * the level count of the delayed schedule of Algorithm 5.
  */
 int32_t or_peel_immediate(int32_t b, int32_t m, int32_t n,
                           const int32_t *pre_ptr, const int32_t *pre_idx,
                           const int32_t *lt_ptr, const int32_t *lt_idx,
                           const uint8_t *erased, const int32_t *order,
-                          uint8_t *unrecovered)
+                          uint8_t *unrecovered, int32_t *n_sweeps)
 {
-    int32_t k_int = b + m, n_con = n + m, recovered = 0;
+    int32_t k_int = b + m, n_con = n + m, recovered = 0, sweeps = 0;
     for (int32_t v = 0; v < k_int; v++) unrecovered[v] = 1;
     int changed = 1;
     while (changed) {
@@ -270,7 +273,9 @@ int32_t or_peel_immediate(int32_t b, int32_t m, int32_t n,
                 changed = 1;
             }
         }
+        if (changed) sweeps++;
     }
+    if (n_sweeps) *n_sweeps = sweeps;
     return recovered;
 }
 

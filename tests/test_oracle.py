@@ -165,15 +165,39 @@ def test_exhaustive_erasures_against_elimination(seed, b, m, n):
                 assert not out[v].any()
         # the peeling fixpoint does not depend on the visiting order
         order = rng.permutation(n + m).astype(np.int32)
-        unrec_imm = oracle.peel_immediate(g, erased, order)
+        unrec_imm, sweeps = oracle.peel_immediate(g, erased, order, with_sweeps=True)
         assert np.array_equal(unrec_imm, path.unrecovered)
+        # immediate updates reach the fixpoint in no more sweeps than the
+        # delayed schedule has levels (Section 3.1: t_m <= t-bar_m)
+        assert sweeps <= path.n_levels
+        _check_path_rules(g, erased, path)
+        # the two-pass decoder: its own rules, never more than the joint one,
+        # never more than elimination, and its bytes are the source
+        out2, path2 = oracle.decode(g, coded, erased, t, oracle.MODE_TWO_PASS)
+        _check_path_rules(g, erased, path2, oracle.MODE_TWO_PASS)
+        rec2 = {v for v in range(k_int) if not path2.unrecovered[v]}
+        assert rec2 <= recovered
+        for v in range(b):
+            if v in rec2:
+                assert np.array_equal(out2[v], data[v])
+            else:
+                assert not out2[v].any()
     assert complete > 0
 
 
 def _check_path_rules(g, erased, path, mode=oracle.MODE_JOINT):
     """Algorithm 5 rules checked level by level: each g had exactly one
     unknown f at the start of its level, f was unknown, each f appears once,
-    and g is the lowest (degree, index) among that level's candidates for f."""
+    g is the lowest (degree, index) among that level's candidates for f, and
+    a level holds every f some candidate offers. After the last level no
+    candidate is left (the fixpoint).
+
+    Joint mode: the candidates are the surviving coded rows and the precode
+    checks. Two-pass mode (founsureDec in Section 2.2: BP on the LT code, then
+    BP on the precode): stage 0 admits only surviving coded rows and runs
+    until a level finds none; from then on only precode checks, until a level
+    finds none; a stage never returns to coded rows. Returns the number of
+    stage-0 levels (the whole path in joint mode)."""
     known = np.zeros(g.k_int, bool)
 
     def vars_of(c):
@@ -182,24 +206,72 @@ def _check_path_rules(g, erased, path, mode=oracle.MODE_JOINT):
         j = c - g.n
         return list(g.pre_idx[g.pre_ptr[j]:g.pre_ptr[j + 1]]) + [g.b + j]
 
-    seen = set()
-    for lvl, pairs in enumerate(path.levels()):
+    def candidates(cons):
         cand = {}
-        for c in range(g.n + g.m):
+        for c in cons:
             if c < g.n and erased[c]:
                 continue
             unk = [v for v in vars_of(c) if not known[v]]
             if len(unk) == 1:
                 cand.setdefault(unk[0], []).append((len(vars_of(c)), c))
-        if mode == oracle.MODE_JOINT:
-            assert {f for f, _ in pairs} == set(cand)
+        return cand
+
+    lt_rows, checks = range(g.n), range(g.n, g.n + g.m)
+    two_pass = mode == oracle.MODE_TWO_PASS
+    stage = 0
+    stage0_levels = None
+    seen = set()
+    for lvl, pairs in enumerate(path.levels()):
+        if two_pass:
+            cand = candidates(lt_rows if stage == 0 else checks)
+            if stage == 0 and not cand:
+                # stage 0 reached its fixpoint: this level opens stage 1
+                stage, stage0_levels = 1, lvl
+                cand = candidates(checks)
+        else:
+            cand = candidates(range(g.n + g.m))
+        assert {f for f, _ in pairs} == set(cand)
         for f, c in pairs:
             assert f not in seen
             seen.add(f)
             assert (len(vars_of(c)), c) == min(cand[f])
+            if two_pass:
+                assert (c < g.n) == (stage == 0)
         for f, _ in pairs:
             known[f] = True
+    if two_pass:
+        if stage == 0:
+            stage0_levels = path.n_levels
+            assert not candidates(lt_rows)
+        assert not candidates(checks)
+    else:
+        assert not candidates(range(g.n + g.m))
+        stage0_levels = path.n_levels
     assert np.array_equal(~known, path.unrecovered.astype(bool))
+    return stage0_levels
+
+
+def _lt_only_graph(g):
+    """The LT layer alone, as a code with k_int data blocks and no precode:
+    its peeling fixpoint is what stage 0 of the two-pass decoder reaches."""
+    return gen.Graph(g.k_int, 0, g.n, np.zeros(1, np.int32), np.zeros(0, np.int32),
+                     np.asarray(g.lt_ptr, np.int32), np.asarray(g.lt_idx, np.int32))
+
+
+def _checks_closure(g, known):
+    """Precode-only peeling from the state ``known`` with immediate updates
+    (plain sets): the fixpoint stage 1 of the two-pass decoder must reach."""
+    known = set(np.nonzero(known)[0].tolist())
+    rows = [set(g.pre_idx[g.pre_ptr[j]:g.pre_ptr[j + 1]].tolist()) | {g.b + j} for j in range(g.m)]
+    changed = True
+    while changed:
+        changed = False
+        for r in rows:
+            unk = r - known
+            if len(unk) == 1:
+                known |= unk
+                changed = True
+    return known
 
 
 def test_dpg_rules_config1_and_success_size():
@@ -232,6 +304,20 @@ def test_precoded_decode_both_modes():
     out_j, path_j = oracle.decode(g, coded, erased, t, oracle.MODE_JOINT)
     out_2, path_2 = oracle.decode(g, coded, erased, t, oracle.MODE_TWO_PASS)
     _check_path_rules(g, erased, path_j)
+    n0 = _check_path_rules(g, erased, path_2, oracle.MODE_TWO_PASS)
+    # stage 0 recovers exactly the LT layer's own peeling fixpoint (visited
+    # in several random orders with immediate updates), and stage 1 exactly
+    # the precode's closure from there
+    lt = _lt_only_graph(g)
+    rng = np.random.default_rng(5)
+    stage0 = np.zeros(g.k_int, bool)
+    for lvl_pairs in path_2.levels()[:n0]:
+        for f, _ in lvl_pairs:
+            stage0[f] = True
+    for _ in range(3):
+        order = rng.permutation(n).astype(np.int32)
+        assert np.array_equal(oracle.peel_immediate(lt, erased, order) == 0, stage0)
+    assert _checks_closure(g, stage0) == set(np.nonzero(path_2.unrecovered == 0)[0].tolist())
     # the joint fixpoint contains whatever the two-pass schedule recovers
     assert np.all(path_j.unrecovered <= path_2.unrecovered)
     for out, path in ((out_j, path_j), (out_2, path_2)):
@@ -281,3 +367,75 @@ def test_empty_and_degenerate_graphs():
                    np.zeros(1, np.int32), np.zeros(0, np.int32))
     out, path = oracle.decode(g0, np.zeros((0, t), np.uint8), np.zeros(0, np.uint8), t)
     assert path.n_pairs == 0 and path.n_levels == 0 and not out.any()
+
+
+def _hand_graph():
+    """b = 3 data blocks (0, 1, 2), m = 2 parities (3, 4), n = 4 coded rows:
+    check 0 = {0, 1} + parity 3 (constraint 4), check 1 = {} + parity 4
+    (constraint 5: an empty check, its parity is the zero block);
+    c0 = {0}, c1 = {0, 1}, c2 = {3, 2}, c3 = {4, 2}; nothing erased."""
+    return gen.Graph(3, 2, 4, np.array([0, 2, 2], np.int32), np.array([0, 1], np.int32),
+                     np.array([0, 1, 3, 5, 7], np.int32),
+                     np.array([0, 0, 1, 3, 2, 4, 2], np.int32))
+
+
+def test_two_pass_and_joint_differ_on_a_hand_worked_graph():
+    """Both schedules worked by hand from Algorithm 5 and the founsureDec
+    description (Section 2.2).
+
+    Joint: level 0 has c0 -> 0 and check 1 -> 4 (degree 1 from the start);
+    level 1 c1 -> 1 and c3 -> 2 (4 is known); level 2 offers 3 through c2
+    (degree 2) and check 0 (degree 3): c2 wins. Everything is recovered.
+
+    Two-pass: stage 0 (coded rows only) takes c0 -> 0, then c1 -> 1, then
+    stops (c2, c3 hold two unknowns each); stage 1 (checks only) takes check
+    0 -> 3 and check 1 -> 4 in one level, then stops. Block 2 stays
+    unrecovered: c2 and c3 now have one unknown each, but the decoder runs BP
+    at most twice and does not return to the coded rows."""
+    g = _hand_graph()
+    t = 16
+    data = np.arange(3 * t, dtype=np.uint8).reshape(3, t) * 7
+    parity, coded = oracle.encode(g, data, t)
+    assert np.array_equal(parity[0], data[0] ^ data[1]) and not parity[1].any()
+    erased = np.zeros(4, np.uint8)
+
+    out_j, pj = oracle.decode(g, coded, erased, t, oracle.MODE_JOINT)
+    assert pj.levels() == [{(0, 0), (4, 5)}, {(1, 1), (2, 3)}, {(3, 2)}]
+    assert pj.n_levels == 3 and not pj.unrecovered.any()
+    assert np.array_equal(out_j, data)
+
+    out_2, p2 = oracle.decode(g, coded, erased, t, oracle.MODE_TWO_PASS)
+    assert p2.levels() == [{(0, 0)}, {(1, 1)}, {(3, 4), (4, 5)}]
+    assert p2.n_levels == 3
+    assert p2.unrecovered.tolist() == [0, 0, 1, 0, 0]
+    assert np.array_equal(out_2[:2], data[:2]) and not out_2[2].any()
+    _, par2 = oracle.peel(g, coded, p2, t, with_parity=True)
+    assert np.array_equal(par2, parity)
+
+    assert _check_path_rules(g, erased, p2, oracle.MODE_TWO_PASS) == 2
+    # Algorithm 1 in index order with immediate updates: the first sweep
+    # decodes 0 (c0), 1 (c1), 3 (check 0, its members now known) and 4
+    # (check 1); c2 and c3 still held two unknowns when visited. The second
+    # sweep decodes 2 (c2); the third changes nothing. Two productive sweeps
+    # against three delayed levels.
+    unrec, sweeps = oracle.peel_immediate(g, erased, np.arange(6, dtype=np.int32),
+                                          with_sweeps=True)
+    assert not unrec.any() and sweeps == 2
+
+
+def test_immediate_sweeps_never_exceed_delayed_levels():
+    """Section 3.1: the delayed schedule (Algorithm 5) converges no sooner
+    than Algorithm 1 with immediate updates, to the same set (t_m <= t-bar_m);
+    on a code of a few hundred blocks, in several visiting orders."""
+    b, m, n = 300, 16, 420
+    g = gen.make_graph(b, m, n, gen.DIST_FINITE40)
+    erased = np.zeros(n, np.uint8)
+    erased[gen.sample_indices(n, gen.round_count(0.1, n), 33)] = 1
+    path = oracle.dpg(g, erased)
+    rng = np.random.default_rng(8)
+    orders = [np.arange(n + m, dtype=np.int32)] + [rng.permutation(n + m).astype(np.int32)
+                                                   for _ in range(3)]
+    for order in orders:
+        unrec, sweeps = oracle.peel_immediate(g, erased, order, with_sweeps=True)
+        assert np.array_equal(unrec, path.unrecovered)
+        assert 1 <= sweeps <= path.n_levels
