@@ -304,6 +304,8 @@ def run_gpu(args):
         tuning[fs.TUNE_GATHER_CTAS] = args.gather_ctas
     if args.l2_hints:
         tuning[fs.TUNE_L2_HINTS] = 1
+    if args.peel_flow:
+        tuning[fs.TUNE_PEEL_FLOW] = 1
 
     st = Stripe(rank, max(args.steps, 1) + args.warmup, device, tuning,
                 overlap=not args.serial_schedule, two_pass=args.two_pass)
@@ -1069,6 +1071,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l2-hints", action="store_true",
                     help="tuning knob: L2 evict-last / evict-first hints")
+    ap.add_argument("--peel-flow", action="store_true",
+                    help="tuning knob: the payload walks the path without level barriers "
+                         "(fewer HBM bytes, more instructions)")
     ap.add_argument("--two-pass", action="store_true",
                     help="decode in the paper's two passes (LT code, then the precode) "
                          "instead of jointly")

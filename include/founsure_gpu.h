@@ -145,6 +145,25 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
  *                        by the decoding schedule: set the knob before
  *                        fs_decode / fs_decode_schedule (a payload without
  *                        the plan reports FS_ERR_INVALID in the workspace)
+ *   FS_TUNE_PEEL_FLOW    1: the slice payload walks the decoding path
+ *                        without a barrier between levels, on a plan made
+ *                        by the decoding schedule: a heavy decoder (more
+ *                        than 8 loads: precode checks, high-degree rows)
+ *                        is gathered in pieces, each as soon as its members
+ *                        exist, while L2 still holds them, and small
+ *                        gathers are packed into full rounds of 8 loads;
+ *                        each gather waits only for the blocks it reads.
+ *                        It reads fewer bytes from HBM (at 4096 x 64 KiB,
+ *                        n = 5400, 20% erased: 0.60 GB against 1.04 GB)
+ *                        but issues more instructions and its plan costs a
+ *                        second one-CTA pass, so it is not the default. It
+ *                        applies to codes of at most 65535 intermediates and
+ *                        constraints, rows of at most 4000 entries and
+ *                        FS_TUNE_PEEL_CTAS = 1, and to paths whose plan fits
+ *                        shared memory; elsewhere the payload walks level by
+ *                        level. Set it before fs_decode / fs_decode_schedule
+ *                        (the schedule makes the plan). 0 (default): level
+ *                        by level
  * Returns FS_ERR_INVALID for an unknown knob or an out-of-range value. Not
  * thread-safe against concurrent hot calls on the same code. */
 #define FS_TUNE_PEEL_CTAS   1
@@ -154,6 +173,7 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
 #define FS_TUNE_ENCODE_SLICES 5
 #define FS_TUNE_ROWS_PER_TICKET 6
 #define FS_TUNE_PEEL_COLUMNS 7
+#define FS_TUNE_PEEL_FLOW    8
 fs_status fs_code_set_tuning(fs_code *code, int knob, int value);
 
 /* Bytes of caller-provided device workspace that op needs. n_items is the

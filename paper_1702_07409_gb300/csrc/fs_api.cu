@@ -197,6 +197,7 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     c->encode_slices = 1;
     c->rows_per_ticket = 16;
     c->peel_columns = 0;
+    c->peel_flow = 0;
     cudaError_t e = cudaGetDevice(&c->device);
     int v = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c->device);
@@ -268,6 +269,10 @@ FS_API fs_status fs_code_set_tuning(fs_code *c, int knob, int value) {
         case FS_TUNE_PEEL_COLUMNS:
             if (value != 0 && value != 1) return FS_ERR_INVALID;
             c->peel_columns = value;
+            return FS_OK;
+        case FS_TUNE_PEEL_FLOW:
+            if (value != 0 && value != 1) return FS_ERR_INVALID;
+            c->peel_flow = value;
             return FS_OK;
     }
     return FS_ERR_INVALID;

@@ -319,9 +319,11 @@ __device__ __forceinline__ void issue_slice(const CUtensorMap *map, const SliceA
     }
 }
 
-__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity) {
+// Waits for the phase with the given parity; false after `rounds` x
+// kSliceWait polls.
+__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity, int rounds = 1) {
     const uint32_t addr = saddr(bar);
-    for (long long i = 0; i < kSliceWait; ++i) {
+    for (long long i = 0; i < kSliceWait * rounds; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -469,9 +471,12 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
             int ok = 1;
             if (t < n_slices) {
                 ok = wait_phase(&s_bar[b], (b ? uses1 : uses0) & 1) ? 1 : 0;
-                if (!ok) {  // a second bounded wait for the copies in flight, then give up
+                if (!ok) {
+                    // give up, but first wait longer (8 bounds) for the copies in
+                    // flight into this buffer; only if that wait expires too does
+                    // the CTA leave with a copy possibly still landing
                     atomicExch(a.status, (int32_t)FS_ERR_TIMEOUT);
-                    wait_phase(&s_bar[b], (b ? uses1 : uses0) & 1);
+                    wait_phase(&s_bar[b], (b ? uses1 : uses0) & 1, 8);
                 }
             }
             s_ok = ok;
@@ -479,7 +484,9 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
         // slice t is in; every warp has left the previous slice (its buffer is free)
         __syncthreads();
         const int32_t t = s_tk[it & 1];
-        if (t >= n_slices || !s_ok) break;  // no copies in flight: the next is issued below
+        // a slice past the end issued no copy; a failed wait was drained above
+        // (as far as its longer bound allows); the next copy is issued below
+        if (t >= n_slices || !s_ok) break;
         if (b) ++uses1;
         else ++uses0;
         if (threadIdx.x == 0) {
@@ -578,9 +585,9 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
             uint4 *slot = slot0 + (size_t)b * buf_words;
             if (threadIdx.x == 0) {
                 int ok = wait_phase(&s_bar[b], (b ? uses1 : uses0) & 1) ? 1 : 0;
-                if (!ok) {  // a second bounded wait for the copies in flight, then give up
+                if (!ok) {  // give up after a longer wait (8 bounds) for the copies in flight
                     atomicExch(status, (int32_t)FS_ERR_TIMEOUT);
-                    wait_phase(&s_bar[b], (b ? uses1 : uses0) & 1);
+                    wait_phase(&s_bar[b], (b ? uses1 : uses0) & 1, 8);
                 }
                 s_ok = ok;
             }

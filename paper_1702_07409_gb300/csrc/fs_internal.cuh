@@ -68,6 +68,8 @@ struct fs_code {
     int rows_per_ticket;  // coded rows per work ticket of the row-gather encode (1..16)
     int peel_columns;     // 1: column payload (every intermediate of a byte column in
                           // shared memory) when the code fits it; 0 (default): slice payload
+    int peel_flow;        // 1: the slice payload walks the path without level barriers
+                          // where its plan fits; 0 (default): level by level
     // slice encode tables (present when sl_slots > 0): every input block has
     // a 16-byte shared-memory slot per byte slice; data block v is slot v,
     // parity j is slot sl_bpad + j. The coded rows are split into sl_parts
@@ -175,10 +177,25 @@ enum {
 //                 (k_int where the entry is f or past the row's end)
 //   col_step[i] = first segment of step i; col_step[n_steps] = all segments.
 //                 A step is at most kColSegMax segments of one level.
+// The dataflow payload's plan (fs_peel.cu): the symbolic pass records the
+// level of every recovered intermediate (flow_lvl) and clears the counters;
+// k_flow_units turns every pair into units of gather work, kept per pair at
+// its padded row's place (flow_raw: its loads from e4 on, flow_uarea /
+// flow_ukey: its units and their keys from e4 / 4 on; a pair of padded degree
+// deg4 has at most deg4 / 4 units and at most deg4 loads), counting units per
+// key in flow_hist; k_flow_place puts the units in key order (flow_units),
+// packs them into batches of at most 8 loads (flow_batch, 16 bytes each; at
+// most one per unit) and lays their loads out in that order (flow_mem):
+//   flow_hdr[0..7] = {units, loads, ok, check slots used, batches, slot
+//                     counter, overflow, 0}
+//   flow_slot[s]   = segments of the check that sums into accumulator s
+constexpr int kFlowSlots = 128;  // check accumulator slots of the dataflow payload
 struct DecodeLayout {
     size_t res, xs, best, known, front_a, front_b, touched, pair_f, pair_g, pair_rec, level_off,
-        level_tab, seg_pair, chunk_pair, unrec_list, parity, col_src, col_step, col_seg, total;
-    int64_t col_max_segs, col_max_steps;
+        level_tab, seg_pair, chunk_pair, unrec_list, parity, col_src, col_step, col_seg, flow_hdr,
+        flow_lvl, flow_hist, flow_ucnt, flow_uarea, flow_ukey, flow_raw, flow_units, flow_batch,
+        flow_mem, flow_slot, total;
+    int64_t col_max_segs, col_max_steps, flow_max_units, flow_max_loads;
 };
 
 static inline DecodeLayout decode_layout(const fs_code *c) {
@@ -208,6 +225,21 @@ static inline DecodeLayout decode_layout(const fs_code *c) {
     L.col_src = o;    o = fs_align256(o + 4 * (K + 1));
     L.col_step = o;   o = fs_align256(o + 4 * ((size_t)L.col_max_steps + 1));
     L.col_seg = o;    o = fs_align256(o + 16 * (size_t)L.col_max_segs);
+    // units: at most e_con4 / 4 (deg4 / 4 per pair); loads: at most e_con4
+    // plus one chain partial per unit
+    L.flow_max_units = (int64_t)c->e_con4 / 4 + 1;
+    L.flow_max_loads = (int64_t)c->e_con4 + L.flow_max_units;
+    L.flow_hdr = o;   o = fs_align256(o + 64);
+    L.flow_lvl = o;   o = fs_align256(o + 2 * (K + 1));
+    L.flow_hist = o;  o = fs_align256(o + 4 * (K + 2));
+    L.flow_ucnt = o;  o = fs_align256(o + 4 * (K + 1));
+    L.flow_uarea = o; o = fs_align256(o + 8 * (size_t)L.flow_max_units);
+    L.flow_ukey = o;  o = fs_align256(o + 2 * (size_t)L.flow_max_units);
+    L.flow_raw = o;   o = fs_align256(o + 2 * (size_t)c->e_con4 + 16);
+    L.flow_units = o; o = fs_align256(o + 8 * (size_t)L.flow_max_units + 16);
+    L.flow_batch = o; o = fs_align256(o + 16 * (size_t)L.flow_max_units + 16);  // uint4 records
+    L.flow_mem = o;   o = fs_align256(o + 2 * (size_t)L.flow_max_loads + 16);
+    L.flow_slot = o;  o = fs_align256(o + 4 * (size_t)kFlowSlots);
     L.total = o;
     return L;
 }

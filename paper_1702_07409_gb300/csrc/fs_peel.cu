@@ -165,6 +165,11 @@ struct DpgArgs {
     int4 *pair_rec, *level_tab;
     uint8_t *unrecovered;
     int32_t *n_unrecovered;
+    // the dataflow plan: header (a new path has no plan yet), the level of
+    // every recovered intermediate, units per key (cleared)
+    int32_t *flow_hdr;
+    uint16_t *flow_lvl;
+    int32_t *flow_hist;
 };
 
 // stage: -1 joint (every surviving coded row and every check), 0 coded rows
@@ -214,6 +219,7 @@ __device__ void emit_level(const DpgArgs &a, LevelCursor &cur, int nt, PairOf pa
             const int32_t p = cur.np + i;
             a.pair_f[p] = f;
             a.pair_g[p] = g;
+            a.flow_lvl[f] = (uint16_t)cur.level;
             const int32_t so = len.y + off.y;
             a.pair_rec[2 * (size_t)p] = make_int4(f, g, len.x + off.x, cnt.z ? len.z + off.z : -1);
             a.pair_rec[2 * (size_t)p + 1] = make_int4(cptr4[g], cnt.x, so, cnt.y);
@@ -265,6 +271,7 @@ __device__ void finish_dpg(const DpgArgs &a, const LevelCursor &cur, const uint8
         *s_cnt = 0;
         *s_cnt_data = 0;
     }
+    for (int32_t l = threadIdx.x; l <= cur.level + 1; l += blockDim.x) a.flow_hist[l] = 0;
     __syncthreads();
     for (int32_t v = threadIdx.x; v < a.k_int; v += blockDim.x) {
         const uint8_t u = known[v] ? 0 : 1;
@@ -279,6 +286,7 @@ __device__ void finish_dpg(const DpgArgs &a, const LevelCursor &cur, const uint8
         *a.n_unrecovered = *s_cnt;
         a.hdr[WS_N_UNREC_DATA] = *s_cnt_data;
         a.hdr[WS_COL_STEPS] = -1;  // no column payload plan for this path (yet)
+        for (int i = 0; i < 8; ++i) a.flow_hdr[i] = 0;  // ... and no dataflow plan
     }
 }
 
@@ -649,6 +657,13 @@ struct PeelArgs {
     int32_t L;  // words of every block per CTA
     int32_t hints;  // 1: gathered / recovered blocks evict-last, coded payloads evict-first
     int32_t *status;
+    // dataflow walk (flow_body): on when 1, on the plan of k_flow_plan
+    int32_t flow;
+    int32_t k_int;
+    const int32_t *fhdr, *fslot;
+    const uint2 *funits;
+    const uint4 *fbatch;
+    const uint16_t *fmem;
 };
 
 __device__ __forceinline__ void xor4(uint4 &a, const uint4 &b) {
@@ -676,10 +691,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  : "memory");
 }
 
-// Waits for the phase with the given parity; false after the bound.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Waits for the phase with the given parity; false after `rounds` x
+// kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int rounds = 1) {
     const uint32_t addr = smem_addr(bar);
-    for (long long i = 0; i < kWaitLimit; ++i) {
+    for (long long i = 0; i < kWaitLimit * rounds; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -824,21 +840,40 @@ __device__ __forceinline__ void peel_body(const PeelArgs &a, int64_t slice) {
                 issue_pairs(a, ltab, l, pairs + l * kStagePairs * kRec, segs + l * kStageSegs,
                             chunks + l * (kStageRecipe / 4), &mb_pairs[l]);
             s_ok = (nl == 0 || mbar_wait(&mb_pairs[0], 0)) ? 1 : 0;
+            if (!s_ok) {
+                // give up, but first wait longer (8 bounds) for the copies of
+                // levels 0 and 1 still in flight
+                mbar_wait(&mb_pairs[0], 0, 8);
+                if (nl > 1) mbar_wait(&mb_pairs[1], 0, 8);
+            }
         }
         __syncthreads();
         if (s_ok && nl > 0) stage_rows(a, ltab, 0, pairs, chunks, rows, w0, lanes);
         cp_async_commit();
+        // thread 0 alone reads and writes fail (a failed prologue stops the
+        // walk at its first level); every thread reads s_ok only after the
+        // barrier that follows thread 0's write
+        int fail = (threadIdx.x == 0 && !s_ok) ? 1 : 0;
         for (int32_t l = 0; l < nl; ++l) {
             const int ps = l % 3, rslot = l & 1;
             // level l's pairs (bulk) and rows (this thread's copies) are in;
             // so are level l+1's pairs, which step 2 reads
             cp_async_wait_all();
-            if (threadIdx.x == 0)
-                s_ok = (mbar_wait(&mb_pairs[ps], (uint32_t)((l / 3) & 1)) &&
-                        (l + 1 >= nl ||
-                         mbar_wait(&mb_pairs[(l + 1) % 3], (uint32_t)(((l + 1) / 3) & 1))))
-                           ? 1
-                           : 0;
+            if (threadIdx.x == 0 && fail) s_ok = 0;
+            if (threadIdx.x == 0 && !fail) {
+                const uint32_t ph0 = (uint32_t)((l / 3) & 1), ph1 = (uint32_t)(((l + 1) / 3) & 1);
+                const bool in0 = mbar_wait(&mb_pairs[ps], ph0);
+                const bool in1 = in0 && (l + 1 >= nl || mbar_wait(&mb_pairs[(l + 1) % 3], ph1));
+                s_ok = in1 ? 1 : 0;
+                if (!in1) {
+                    // give up, but first wait longer (8 bounds) for each copy not
+                    // yet seen to land (levels l and l+1; l+2's is not issued
+                    // yet); only if that wait expires too does the CTA leave with
+                    // a copy possibly still landing in its shared memory
+                    if (!in0) mbar_wait(&mb_pairs[ps], ph0, 8);
+                    if (l + 1 < nl) mbar_wait(&mb_pairs[(l + 1) % 3], ph1, 8);
+                }
+            }
             __syncthreads();  // level l-1 is written; level l's stages are in
             if (!s_ok) break;
             const int32_t *pc = pairs + ps * kStagePairs * kRec;
@@ -916,7 +951,681 @@ __device__ __forceinline__ void peel_body(const PeelArgs &a, int64_t slice) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// dataflow payload
+//
+// The level walk above waits for a whole level at a barrier, and its gathers
+// reach far back: a decoder of degree 19, or a precode check with ~97
+// members, reads blocks recovered dozens of levels earlier, which L2 no
+// longer holds (at the precoded stripe 45% of the coded-row gathers and 75%
+// of the check gathers reach back past more than 62 MB of newer output).
+// The dataflow walk gathers the members of such heavy pairs while they are
+// fresh, and packs small gathers into full rounds of loads. Its plan:
+//   - a light pair (at most 8 loads: c_g when g is a coded row, then the
+//     other members of g) is one whole unit; its key is its level;
+//   - a heavy pair has its members sorted by the level that recovered them
+//     (up to kFlowSortMax) and cut into segments of at least 8 loads (the
+//     first one starting with c_g); a segment's key is 1 + the highest
+//     level among its members, so it can run as soon as they exist:
+//       * a precode check sums its segments into a shared-memory
+//         accumulator of its own (kFlowSlots of them); the segment that
+//         completes the count writes x_f;
+//       * any other heavy pair chains its segments through x_f itself:
+//         segment r > 0 loads the partial sum the previous one wrote, adds
+//         its members and writes it back. Keys are made non-decreasing and
+//         segments with equal keys merged, so the keys of a chain rise
+//         strictly;
+//   - units are put in key order and consecutive units of one key packed
+//     into batches of at most 8 loads (one round of loads in flight).
+// Every unit reads only pairs whose units all have smaller keys (a pair of
+// level l has its members in levels below l, hence keys at most l), and a
+// chain segment also reads its predecessor, which has a smaller key; units
+// of one key never read each other. In the payload (flow_body) warp w takes
+// batches w, w + 32, ... and waits, on shared-memory ready flags, for what
+// each batch reads. The batch at the lowest position not yet done reads only
+// finished work and its warp is working on it (a warp takes its batches in
+// order), so the walk always advances; every wait is bounded all the same
+// and an expired wait stops the CTA with FS_ERR_TIMEOUT. Each (pair, word) of
+// the result is the XOR of the same terms as in the level walk.
+
+constexpr int kFlowSeg = 8;           // loads of one segment (at least); of one batch (at most)
+constexpr int kFlowSortMax = 256;     // heavy members sorted by level up to this count
+constexpr int kFlowChain = 120;       // chain segments of one pair at most
+constexpr int kFlowMaxDeg = 4000;     // largest constraint degree (12-bit load counts)
+constexpr int kFlowUnitThreads = 256;
+constexpr long long kFlowWaitLimit = 1ll << 22;  // polls of a ready flag
+
+// unit record: x = f | hasg << 16 | kind << 17 | aux << 19 | last << 27,
+//              y = first load | member loads << 20
+// (k_flow_units writes the first load's place in flow_raw, k_flow_place its
+// place in flow_mem)
+enum { kUnitWhole = 0, kUnitSlot = 1, kUnitChain = 2 };
+constexpr uint32_t kMoffMask = (1u << 20) - 1;
+constexpr uint8_t kReadyFinal = 0x80;  // ready flag: x_f is final; low bits: chain segments done
+enum { kFhUnits = 0, kFhLoads = 1, kFhOk = 2, kFhSlots = 3, kFhBatches = 4, kFhSlotCtr = 5,
+       kFhOverflow = 6 };
+
+// Loads of a unit: c_g, the chain's partial sum, its members; a unit with
+// none (a check of no members decoding its parity: the zero block) keeps one
+// slot that loads nothing.
+__device__ __forceinline__ int unit_slots(uint2 r) {
+    const int hasg = (int)((r.x >> 16) & 1u), kind = (int)((r.x >> 17) & 3u);
+    const int aux = (int)((r.x >> 19) & 0xffu);
+    const int sl = hasg + ((kind == kUnitChain && aux > 0) ? 1 : 0) + (int)(r.y >> 20);
+    return sl > 0 ? sl : 1;
+}
+
+struct FlowUnitArgs {
+    const int32_t *hdr;
+    const int4 *pair_rec;
+    const int32_t *con_ptr, *con_idx4;
+    const uint16_t *lvl;
+    int32_t n, slot_cap;
+    int32_t *fhdr, *hist, *ucnt, *slot_nseg;
+    uint2 *uarea;
+    uint16_t *ukey, *raw;
+};
+
+// Every pair of the path into units, one warp per pair (a light pair is
+// done by lane 0; a heavy one by the whole warp, which sorts its members).
+__global__ void __launch_bounds__(kFlowUnitThreads) k_flow_units(FlowUnitArgs a) {
+    __shared__ int s_key[kFlowUnitThreads / 32][128];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int32_t P = a.hdr[WS_N_PAIRS], NL = a.hdr[WS_N_LEVELS];
+    const int32_t p = blockIdx.x * (kFlowUnitThreads / 32) + wid;
+    if (p >= P) return;  // whole warps leave; no block barrier below
+    int *skey = s_key[wid];
+    {
+        const int4 r0 = a.pair_rec[2 * (size_t)p];
+        const int32_t f = r0.x, g = r0.y, e4 = a.pair_rec[2 * (size_t)p + 1].x;
+        const int32_t deg = __ldg(a.con_ptr + g + 1) - __ldg(a.con_ptr + g);
+        const int hasg = g < a.n ? 1 : 0, loads = hasg + deg - 1;
+        if (loads <= kFlowSeg) {
+            // light: its loads in row order (g first) and one whole unit
+            if (lane == 0) {
+                int w = e4;
+                if (hasg) a.raw[w++] = (uint16_t)g;
+                const int4 *row = reinterpret_cast<const int4 *>(a.con_idx4 + e4);
+                int4 q4[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) q4[i] = 4 * i < deg ? __ldg(row + i) : make_int4(-1, -1, -1, -1);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int32_t hv[4] = {q4[i].x, q4[i].y, q4[i].z, q4[i].w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (4 * i + t < deg && hv[t] != f) a.raw[w++] = (uint16_t)hv[t];
+                }
+                const int key = min((int)a.lvl[f], NL);
+                a.uarea[e4 >> 2] = make_uint2((uint32_t)f | ((uint32_t)hasg << 16),
+                                              (uint32_t)e4 | ((uint32_t)(deg - 1) << 20));
+                a.ukey[e4 >> 2] = (uint16_t)key;
+                a.ucnt[p] = 1;
+                atomicAdd(a.hist + key, 1);
+            }
+            return;
+        }
+    }
+    {
+        const int4 r0 = a.pair_rec[2 * (size_t)p];
+        const int32_t f = r0.x, g = r0.y, e4 = a.pair_rec[2 * (size_t)p + 1].x;
+        const int32_t deg = __ldg(a.con_ptr + g + 1) - __ldg(a.con_ptr + g);
+        const int hasg = g < a.n ? 1 : 0, d = deg - 1, loads = hasg + d;
+        // a check sums into a slot while slots last; the rest chain
+        int slot = -1;
+        if (!hasg) {
+            if (lane == 0) slot = atomicAdd(a.fhdr + kFhSlotCtr, 1);
+            slot = __shfl_sync(0xffffffffu, slot, 0);
+            if (slot >= a.slot_cap) slot = -1;
+        }
+        int S = kFlowSeg;
+        if (slot < 0) S = max(S, (loads + kFlowChain - 1) / kFlowChain);
+        const int nseg = (loads + S - 1) / S;
+        if (hasg && lane == 0) a.raw[e4] = (uint16_t)g;
+        for (int s = lane; s < 128; s += 32) skey[s] = 0;
+        __syncwarp();
+        // the member at load position q belongs to segment q / S, whose key
+        // is 1 + the highest level among its members
+        if (deg <= kFlowSortMax) {
+            // element i of this lane is row entry lane + 32 i; its key
+            // (level, index) ranks it among the d members (keys are distinct;
+            // the f entry and lanes past the row hold the largest key)
+            uint32_t key[kFlowSortMax / 32];
+#pragma unroll
+            for (int i = 0; i < kFlowSortMax / 32; ++i) {
+                const int j = lane + 32 * i;
+                key[i] = 0xFFFFFFFFu;
+                if (j < deg) {
+                    const int32_t h = __ldg(a.con_idx4 + e4 + j);
+                    if (h != f) key[i] = ((uint32_t)a.lvl[h] << 16) | (uint32_t)h;
+                }
+            }
+            int rk[kFlowSortMax / 32];
+#pragma unroll
+            for (int i = 0; i < kFlowSortMax / 32; ++i) rk[i] = 0;
+#pragma unroll
+            for (int i2 = 0; i2 < kFlowSortMax / 32; ++i2) {
+                if (32 * i2 >= deg) break;
+                for (int q = 0; q < 32; ++q) {
+                    const uint32_t kq = __shfl_sync(0xffffffffu, key[i2], q);
+#pragma unroll
+                    for (int i = 0; i < kFlowSortMax / 32; ++i) rk[i] += kq < key[i] ? 1 : 0;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < kFlowSortMax / 32; ++i) {
+                if (key[i] == 0xFFFFFFFFu) continue;
+                const int q = hasg + rk[i];
+                a.raw[e4 + q] = (uint16_t)(key[i] & 0xffffu);
+                if (q / S < 128) atomicMax(skey + q / S, min((int)(key[i] >> 16) + 1, NL));
+            }
+        } else {
+            // row order, compacted by ballot
+            int w = 0;
+            for (int32_t j0 = 0; j0 < deg; j0 += 32) {
+                const int32_t h = j0 + lane < deg ? __ldg(a.con_idx4 + e4 + j0 + lane) : f;
+                const unsigned keep = __ballot_sync(0xffffffffu, h != f);
+                if (h != f) {
+                    const int q = hasg + w + __popc(keep & ((1u << lane) - 1));
+                    a.raw[e4 + q] = (uint16_t)h;
+                    if (q / S < 128) atomicMax(skey + q / S, min((int)a.lvl[h] + 1, NL));
+                }
+                w += __popc(keep);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const int ub = e4 >> 2;
+            if (nseg > 128) {
+                atomicExch(a.fhdr + kFhOverflow, 1);  // more segments than the key table
+                a.ucnt[p] = 0;
+            } else if (slot >= 0) {
+                for (int s = 0; s < nseg; ++s) {
+                    const int s0 = s * S, s1 = min(loads, s0 + S);
+                    const int hg = (s == 0) ? hasg : 0;
+                    a.uarea[ub + s] = make_uint2((uint32_t)f | ((uint32_t)hg << 16) |
+                                                     ((uint32_t)kUnitSlot << 17) | ((uint32_t)slot << 19),
+                                                 (uint32_t)(e4 + s0) | ((uint32_t)(s1 - s0 - hg) << 20));
+                    a.ukey[ub + s] = (uint16_t)skey[s];
+                    atomicAdd(a.hist + skey[s], 1);
+                }
+                a.slot_nseg[slot] = nseg;
+                a.ucnt[p] = nseg;
+            } else {
+                // chain: keys made non-decreasing (a later key is still at
+                // most the pair's level), runs of equal keys merged
+                for (int s = 1; s < nseg; ++s) skey[s] = max(skey[s], skey[s - 1]);
+                int runs = 0;
+                for (int s = 0; s < nseg; ++s) runs += (s == 0 || skey[s] != skey[s - 1]) ? 1 : 0;
+                int r = -1;
+                for (int s = 0; s < nseg; ++s) {
+                    if (s > 0 && skey[s] == skey[s - 1]) continue;
+                    ++r;
+                    int e = s;
+                    while (e + 1 < nseg && skey[e + 1] == skey[s]) ++e;
+                    const int s0 = s * S, s1 = min(loads, (e + 1) * S);
+                    const int hg = (s == 0) ? hasg : 0;
+                    a.uarea[ub + r] = make_uint2((uint32_t)f | ((uint32_t)hg << 16) |
+                                                     ((uint32_t)kUnitChain << 17) | ((uint32_t)r << 19) |
+                                                     ((r == runs - 1) ? (1u << 27) : 0u),
+                                                 (uint32_t)(e4 + s0) | ((uint32_t)(s1 - s0 - hg) << 20));
+                    a.ukey[ub + r] = (uint16_t)skey[s];
+                    atomicAdd(a.hist + skey[s], 1);
+                }
+                a.ucnt[p] = runs;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+struct FlowPlaceArgs {
+    const int32_t *hdr, *hist, *ucnt;
+    const int4 *pair_rec;
+    const uint2 *uarea;
+    const uint16_t *ukey, *raw;  // read-only here (written by k_flow_units)
+    int32_t *fhdr;
+    uint2 *units;
+    uint4 *batches;
+    uint16_t *mem;
+    int32_t cap_bytes;   // shared memory the payload has for units, batches and loads
+    int32_t slot_cap;
+    int32_t smem_bytes;  // dynamic shared memory of this kernel
+};
+
+// Block-wide exclusive scan of one counter; *tot receives the sum. Every
+// thread calls it; s_w holds 32 ints of scratch.
+__device__ int flow_block_scan(int x, int *tot, int *s_w) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    int v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) s_w[wid] = v;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int j = 0; j < nw; ++j) {
+        const int t = s_w[j];
+        before += j < wid ? t : 0;
+        all += t;
+    }
+    __syncthreads();  // s_w may be reused after this
+    *tot = all;
+    return before + v - x;
+}
+
+// The units in key order, their batches and their loads in batch order.
+__global__ void __launch_bounds__(1024, 1) k_flow_place(FlowPlaceArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_w[32];
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int32_t P = a.hdr[WS_N_PAIRS], NL = a.hdr[WS_N_LEVELS];
+    if (a.fhdr[kFhOverflow]) return;  // no plan: the payload walks level by level
+    auto up16 = [](int x) { return (x + 15) & ~15; };
+    // keys 0..NL: their first unit (kst), a placement cursor (kcur), their
+    // batch count then first batch (kb)
+    const int nk = NL + 1;
+    int *kst = reinterpret_cast<int *>(smem);
+    int *kcur = kst + nk + 1;
+    int *kb = kcur + nk + 1;
+    const int per = (nk + T - 1) / T;
+    int c = 0;
+    for (int k = tid * per; k < min(nk, (tid + 1) * per); ++k) c += a.hist[k];
+    int U;
+    int run = flow_block_scan(c, &U, s_w);
+    for (int k = tid * per; k < min(nk, (tid + 1) * per); ++k) {
+        kst[k] = run;
+        kcur[k] = 0;
+        run += a.hist[k];
+    }
+    if (tid == 0) kst[nk] = U;
+    const int o_srec = up16(4 * 3 * (nk + 1));
+    const int o_uoff = o_srec + up16(8 * U);
+    if (o_uoff + up16(4 * (U + 1)) > a.smem_bytes) return;
+    uint2 *srec = reinterpret_cast<uint2 *>(smem + o_srec);
+    int *uoff = reinterpret_cast<int *>(smem + o_uoff);
+    __syncthreads();
+    // every unit at its key's place (any order inside a key)
+    for (int32_t p = tid; p < P; p += T) {
+        const int32_t ub = __ldg(&a.pair_rec[2 * (size_t)p + 1].x) >> 2;
+        const int cu = __ldg(a.ucnt + p);
+        for (int i = 0; i < cu; ++i) {
+            const int k = __ldg(a.ukey + ub + i);
+            srec[kst[k] + atomicAdd(kcur + k, 1)] = __ldg(a.uarea + ub + i);
+        }
+    }
+    __syncthreads();
+    // the loads of the units in this order
+    const int upt = (U + T - 1) / T;
+    c = 0;
+    for (int u = tid * upt; u < min(U, (tid + 1) * upt); ++u) c += unit_slots(srec[u]);
+    int M;
+    run = flow_block_scan(c, &M, s_w);
+    for (int u = tid * upt; u < min(U, (tid + 1) * upt); ++u) {
+        uoff[u] = run;
+        run += unit_slots(srec[u]);
+    }
+    if (tid == 0) uoff[U] = M;
+    __syncthreads();
+    // batches: consecutive units of one key, at most kFlowSeg loads and
+    // units each (a unit of more loads alone)
+    c = 0;
+    for (int k = tid * per; k < min(nk, (tid + 1) * per); ++k) {
+        int nb = 0, load = kFlowSeg + 1, cnt = kFlowSeg;
+        for (int u = kst[k]; u < kst[k + 1]; ++u) {
+            const int sl = unit_slots(srec[u]);
+            if (load + sl > kFlowSeg || cnt == kFlowSeg) {
+                ++nb;
+                load = 0;
+                cnt = 0;
+            }
+            load += sl;
+            ++cnt;
+        }
+        kb[k] = nb;
+        c += nb;
+    }
+    int NB;
+    run = flow_block_scan(c, &NB, s_w);
+    const bool fits = up16(8 * U) + up16(16 * NB) + up16(2 * M) <= a.cap_bytes && M <= (int)kMoffMask &&
+                      U < 65536;
+    for (int k = tid * per; k < min(nk, (tid + 1) * per); ++k) {
+        const int nb = kb[k];
+        kb[k] = run;
+        run += nb;
+    }
+    __syncthreads();
+    if (!fits) return;
+    // batch record: {u0 | units << 16 | loads << 20, first load, masks over
+    // its loads (a batch of at most kFlowSeg): c_g | partial sum << 8 | last
+    // load of a unit << 16 (a dummy load of a unit without loads has both of
+    // the first two bits), 0}
+    auto put_batch = [&](int b, int u0, int cnt, int load) {
+        uint32_t cm = 0, pm = 0, em = 0;
+        if (load <= kFlowSeg) {
+            int j = 0;
+            for (int u = u0; u < u0 + cnt; ++u) {
+                const uint2 r = srec[u];
+                const int hasg = (int)((r.x >> 16) & 1u), kind = (int)((r.x >> 17) & 3u);
+                const int aux = (int)((r.x >> 19) & 0xffu);
+                const int sl = unit_slots(r);
+                if (hasg + ((kind == kUnitChain && aux > 0) ? 1 : 0) + (int)(r.y >> 20) == 0) {
+                    cm |= 1u << j;
+                    pm |= 1u << j;
+                } else {
+                    if (hasg) cm |= 1u << j;
+                    if (kind == kUnitChain && aux > 0) pm |= 1u << (j + hasg);
+                }
+                j += sl;
+                em |= 1u << (j - 1);
+            }
+        }
+        a.batches[b] = make_uint4((uint32_t)u0 | ((uint32_t)cnt << 16) | ((uint32_t)load << 20),
+                                  (uint32_t)uoff[u0], cm | (pm << 8) | (em << 16), 0u);
+    };
+    for (int k = tid * per; k < min(nk, (tid + 1) * per); ++k) {
+        int b = kb[k] - 1, load = kFlowSeg + 1, cnt = kFlowSeg, u0 = 0;
+        for (int u = kst[k]; u < kst[k + 1]; ++u) {
+            const int sl = unit_slots(srec[u]);
+            if (load + sl > kFlowSeg || cnt == kFlowSeg) {
+                if (b >= kb[k]) put_batch(b, u0, cnt, load);
+                ++b;
+                load = 0;
+                cnt = 0;
+                u0 = u;
+            }
+            load += sl;
+            ++cnt;
+        }
+        if (b >= kb[k]) put_batch(b, u0, cnt, load);
+    }
+    // the units with their loads' new place; the loads: c_g, the chain's
+    // partial sum (x_f), then the members
+    for (int u = tid; u < U; u += T) {
+        const uint2 r = srec[u];
+        const int hasg = (int)((r.x >> 16) & 1u), kind = (int)((r.x >> 17) & 3u);
+        const int aux = (int)((r.x >> 19) & 0xffu), cnt = (int)(r.y >> 20);
+        const int from = (int)(r.y & kMoffMask);
+        int o = uoff[u];
+        if (hasg + ((kind == kUnitChain && aux > 0) ? 1 : 0) + cnt == 0) a.mem[o] = 0;  // dummy
+        if (hasg) a.mem[o++] = __ldg(a.raw + from);
+        if (kind == kUnitChain && aux > 0) a.mem[o++] = (uint16_t)(r.x & 0xffffu);
+        for (int j0 = 0; j0 < cnt; j0 += 8) {
+            uint16_t v[8];  // loads issued together
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = j0 + j < cnt ? __ldg(a.raw + from + hasg + j0 + j) : 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (j0 + j < cnt) a.mem[o + j0 + j] = v[j];
+        }
+        a.units[u] = make_uint2(r.x, (uint32_t)uoff[u] | (r.y & ~kMoffMask));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        a.fhdr[kFhUnits] = U;
+        a.fhdr[kFhLoads] = M;
+        a.fhdr[kFhBatches] = NB;
+        a.fhdr[kFhSlots] = min(a.fhdr[kFhSlotCtr], a.slot_cap);
+        __threadfence();
+        a.fhdr[kFhOk] = 1;
+    }
+}
+
+// Writes x_f of a finished check from its accumulator and marks it final
+// (the whole warp; every segment fenced before counting).
+__device__ __forceinline__ void flow_finish_slot(const PeelArgs &a, uint2 r, uint4 *accs, uint8_t *ready,
+                                                 int64_t w0, int lanes, int L) {
+    const int lane = threadIdx.x & 31;
+    const int32_t f = (int32_t)(r.x & 0xffffu);
+    __threadfence_block();
+    const volatile uint4 *sa = accs + (size_t)((r.x >> 19) & 0xffu) * L;
+    for (int k = lane; k < lanes; k += 32) {
+        const uint4 v = make_uint4(sa[k].x, sa[k].y, sa[k].z, sa[k].w);
+        block_ptr(a, f)[w0 + k] = v;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence_block();
+        *(volatile uint8_t *)(ready + f) = kReadyFinal;
+    }
+}
+
+// One unit of ns > kFlowSeg loads (ml[0..ns): c_g, the chain's partial sum,
+// members), gathered kFlowSeg at a time. Returns false when its wait expired
+// (the CTA stops).
+__device__ bool flow_big_unit(const PeelArgs &a, uint2 r, const uint16_t *ml, int ns,
+                              const volatile uint8_t *rdy, uint8_t *ready, uint4 *accs, int32_t *done,
+                              int64_t w0, int lanes, int L, int *s_abort) {
+    const int lane = threadIdx.x & 31;
+    const int32_t f = (int32_t)(r.x & 0xffffu);
+    const int hasg = (int)((r.x >> 16) & 1u), kind = (int)((r.x >> 17) & 3u);
+    const int aux = (int)((r.x >> 19) & 0xffu);
+    const int part = (kind == kUnitChain && aux > 0) ? 1 : 0;  // load hasg is the partial sum
+    bool ok = false;
+    for (long long it = 0; it < kFlowWaitLimit; ++it) {
+        bool mine = true;
+        for (int j = lane; j < ns; j += 32) {
+            if (hasg && j == 0) continue;
+            if (part && j == hasg) mine = mine && (rdy[f] & 0x7f) == aux;
+            else mine = mine && (rdy[ml[j]] & kReadyFinal) != 0;
+        }
+        ok = __all_sync(0xffffffffu, mine);
+        if (ok || __any_sync(0xffffffffu, *(volatile int *)s_abort != 0)) break;  // warp-uniform exit
+        __nanosleep(32);
+    }
+    if (!ok) {
+        if (lane == 0) {
+            atomicExch(a.status, FS_ERR_TIMEOUT);
+            *s_abort = 1;
+        }
+        return false;
+    }
+    __syncwarp();
+    __threadfence_block();
+    for (int k = lane; k < lanes; k += 32) {
+        const int64_t w = w0 + k;
+        uint4 acc = make_uint4(0, 0, 0, 0);
+        for (int j0 = 0; j0 < ns; j0 += kFlowSeg) {
+            uint4 x[kFlowSeg];
+#pragma unroll
+            for (int j = 0; j < kFlowSeg; ++j) {
+                const int jj = j0 + j;
+                x[j] = make_uint4(0, 0, 0, 0);
+                if (jj < ns) {
+                    if (hasg && jj == 0) x[j] = __ldg(a.coded + (int64_t)ml[0] * a.tw + w);
+                    else x[j] = block_ptr(a, ml[jj])[w];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kFlowSeg; ++j) xor4(acc, x[j]);
+        }
+        if (kind == kUnitSlot) xor_shared(accs + (size_t)aux * L + k, acc);
+        else block_ptr(a, f)[w] = acc;
+    }
+    __syncwarp();
+    int fin = 0;
+    if (lane == 0) {
+        __threadfence_block();
+        if (kind == kUnitWhole) *(volatile uint8_t *)(ready + f) = kReadyFinal;
+        else if (kind == kUnitChain)
+            *(volatile uint8_t *)(ready + f) = ((r.x >> 27) & 1u) ? kReadyFinal : (uint8_t)(aux + 1);
+        else fin = atomicSub(done + aux, 1) == 1 ? 1 : 0;
+    }
+    if (__shfl_sync(0xffffffffu, fin, 0)) flow_finish_slot(a, r, accs, ready, w0, lanes, L);
+    return true;
+}
+
+// Runs the payload on the plan; returns false (the same answer in every
+// thread, before anything is written to global memory) when there is no
+// plan, and the caller walks level by level.
+__device__ bool flow_body(const PeelArgs &a, int64_t slice) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_abort;
+    const int32_t *fh = a.fhdr;
+    if (fh[kFhOk] != 1) return false;
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = T >> 5;
+    const int32_t K = a.k_int, U = fh[kFhUnits], M = fh[kFhLoads], NS = fh[kFhSlots];
+    const int32_t NB = fh[kFhBatches];
+    const int L = a.L;
+    const int64_t w0 = slice * L;
+    const int lanes = (int)min((int64_t)L, a.tw - w0);
+    auto up16 = [](int x) { return (x + 15) & ~15; };
+    // shared layout: ready[K], units[U], batches[NB], mem[M], done[NS], accs[NS][L]
+    uint8_t *ready = smem;
+    const int o_units = up16(K);
+    const int o_batch = o_units + up16(8 * U);
+    const int o_mem = o_batch + up16(16 * NB);
+    const int o_done = o_mem + up16(2 * M);
+    const int o_acc = o_done + up16(4 * NS);
+    uint2 *units = reinterpret_cast<uint2 *>(smem + o_units);
+    uint4 *batches = reinterpret_cast<uint4 *>(smem + o_batch);
+    uint16_t *mem = reinterpret_cast<uint16_t *>(smem + o_mem);
+    int32_t *done = reinterpret_cast<int32_t *>(smem + o_done);
+    uint4 *accs = reinterpret_cast<uint4 *>(smem + o_acc);
+    // the plan into shared memory (16-byte copies; the arrays are padded)
+    {
+        const int4 *su = reinterpret_cast<const int4 *>(a.funits);
+        for (int i = tid; i < up16(8 * U) / 16; i += T) reinterpret_cast<int4 *>(units)[i] = su[i];
+        for (int i = tid; i < NB; i += T) batches[i] = a.fbatch[i];
+        const int4 *sm = reinterpret_cast<const int4 *>(a.fmem);
+        for (int i = tid; i < up16(2 * M) / 16; i += T) reinterpret_cast<int4 *>(mem)[i] = sm[i];
+    }
+    for (int i = tid; i < up16(K) / 16; i += T) reinterpret_cast<int4 *>(ready)[i] = make_int4(0, 0, 0, 0);
+    for (int i = tid; i < NS; i += T) done[i] = a.fslot[i];
+    for (int i = tid; i < NS * L; i += T) accs[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) s_abort = 0;
+    __syncthreads();
+
+    const volatile uint8_t *rdy = ready;
+    for (int b = wid; b < NB; b += nw) {
+        if (__any_sync(0xffffffffu, *(volatile int *)&s_abort != 0)) break;  // warp-uniform
+        const uint4 br = batches[b];
+        const int u0 = (int)(br.x & 0xffffu), nu = (int)((br.x >> 16) & 15u);
+        const int ns = (int)((br.x >> 20) & 0xfffu), mo = (int)br.y;
+        if (ns > kFlowSeg) {
+            // one unit of more loads than a round (alone in its batch)
+            if (!flow_big_unit(a, units[u0], mem + mo, ns, rdy, ready, accs, done, w0, lanes, L,
+                               &s_abort))
+                break;
+            continue;
+        }
+        // lane j < ns owns load j of the batch: its block, its kind (0 member,
+        // 1 coded row, 2 the chain's partial sum, 3 nothing), its unit and
+        // whether it is its unit's last load (from the batch's masks)
+        int id = 0, typ = 0, ui = 0, endu = 0, need = 0;
+        if (lane < ns) {
+            const uint32_t bit = 1u << lane, em = (br.z >> 16) & 0xffu;
+            id = mem[mo + lane];
+            typ = ((br.z & bit) ? 1 : 0) | (((br.z >> 8) & bit) ? 2 : 0);
+            endu = (em & bit) ? 1 : 0;
+            ui = __popc(em & (bit - 1));
+            if (typ == 2) need = (int)((units[u0 + ui].x >> 19) & 0xffu);
+        }
+        // wait for every block the batch reads
+        bool ok = false;
+        for (long long it = 0; it < kFlowWaitLimit; ++it) {
+            bool mine = true;
+            if (lane < ns) {
+                if (typ == 0) mine = (rdy[id] & kReadyFinal) != 0;
+                else if (typ == 2) mine = (rdy[id] & 0x7f) == need;
+            }
+            ok = __all_sync(0xffffffffu, mine);
+            if (ok || __any_sync(0xffffffffu, *(volatile int *)&s_abort != 0)) break;  // warp-uniform
+            __nanosleep(32);
+        }
+        if (!ok) {
+            if (lane == 0) {
+                atomicExch(a.status, FS_ERR_TIMEOUT);
+                s_abort = 1;
+            }
+            break;
+        }
+        __syncwarp();  // the watchers' reads come before every lane's loads
+        __threadfence_block();
+        // every lane learns every load of the batch (all 32 lanes here:
+        // the word loop below leaves out the lanes past the slice)
+        // load j: block | kind << 16 | last of its unit << 18 | unit << 19
+        uint32_t jl[kFlowSeg];
+#pragma unroll
+        for (int j = 0; j < kFlowSeg; ++j)
+            jl[j] = __shfl_sync(0xffffffffu,
+                                (uint32_t)id | ((uint32_t)typ << 16) | ((uint32_t)endu << 18) |
+                                    ((uint32_t)ui << 19),
+                                j);
+        for (int k = lane; k < lanes; k += 32) {
+            const int64_t w = w0 + k;
+            uint4 x[kFlowSeg];  // the batch's loads, all in flight at once
+#pragma unroll
+            for (int j = 0; j < kFlowSeg; ++j) {
+                x[j] = make_uint4(0, 0, 0, 0);
+                if (j < ns) {
+                    const int t = (int)((jl[j] >> 16) & 3u), jid = (int)(jl[j] & 0xffffu);
+                    if (t == 1) x[j] = __ldg(a.coded + (int64_t)jid * a.tw + w);
+                    else if (t != 3) x[j] = block_ptr(a, jid)[w];
+                }
+            }
+            uint4 acc = make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int j = 0; j < kFlowSeg; ++j) {
+                const int je = (int)((jl[j] >> 18) & 1u);
+                const int jui = (int)(jl[j] >> 19);
+                if (j < ns) {
+                    xor4(acc, x[j]);
+                    if (je) {
+                        const uint2 r = units[u0 + jui];
+                        const int32_t f = (int32_t)(r.x & 0xffffu);
+                        if (((r.x >> 17) & 3u) == kUnitSlot)
+                            xor_shared(accs + (size_t)((r.x >> 19) & 0xffu) * L + k, acc);
+                        else
+                            block_ptr(a, f)[w] = acc;
+                        acc = make_uint4(0, 0, 0, 0);
+                    }
+                }
+            }
+        }
+        // release: every lane's writes come before the fences and flags
+        __syncwarp();
+        int fin = 0;
+        if (lane < nu) {
+            const uint2 r = units[u0 + lane];
+            const int32_t f = (int32_t)(r.x & 0xffffu);
+            const int kind = (int)((r.x >> 17) & 3u), aux = (int)((r.x >> 19) & 0xffu);
+            __threadfence_block();
+            if (kind == kUnitWhole) *(volatile uint8_t *)(ready + f) = kReadyFinal;
+            else if (kind == kUnitChain)
+                *(volatile uint8_t *)(ready + f) = ((r.x >> 27) & 1u) ? kReadyFinal : (uint8_t)(aux + 1);
+            else fin = atomicSub(done + aux, 1) == 1 ? 1 : 0;
+        }
+        // a check whose last segment this was: its sum is complete (every
+        // other segment fenced before counting)
+        unsigned fins = __ballot_sync(0xffffffffu, fin != 0);
+        while (fins) {
+            const int i = __ffs(fins) - 1;
+            fins &= fins - 1;
+            flow_finish_slot(a, units[u0 + i], accs, ready, w0, lanes, L);
+        }
+    }
+    __syncthreads();
+    // unrecovered data blocks read as zero
+    const int32_t nu = a.hdr[WS_N_UNREC_DATA];
+    for (int32_t it = tid; it < nu * lanes; it += T) {
+        const int32_t q = it / lanes, lane2 = it - q * lanes;
+        a.data[(int64_t)a.unrec_list[q] * a.tw + w0 + lane2] = make_uint4(0, 0, 0, 0);
+    }
+    return true;
+}
+
+// The level walk alone; k_peel_flow is the dataflow walk (its own kernel, so
+// its registers do not weigh on the level walk), which falls back to the
+// level walk when the path has no plan.
 __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) { peel_body(a, blockIdx.x); }
+
+__global__ void __launch_bounds__(kPeelThreads, 1) k_peel_flow(PeelArgs a) {
+    if (flow_body(a, blockIdx.x)) return;
+    peel_body(a, blockIdx.x);
+}
 
 // one CTA per (stripe, slice) item of a batch
 __global__ void __launch_bounds__(kPeelThreads, 1) k_peel_batch(const PeelArgs *as, const int2 *items) {
@@ -969,6 +1678,9 @@ DpgArgs dpg_args(const fs_code *c, const uint8_t *erased, uint8_t *ws, uint8_t *
     a.hdr = reinterpret_cast<int32_t *>(ws);
     a.unrecovered = unrecovered;
     a.n_unrecovered = n_unrecovered;
+    a.flow_hdr = reinterpret_cast<int32_t *>(ws + L.flow_hdr);
+    a.flow_lvl = reinterpret_cast<uint16_t *>(ws + L.flow_lvl);
+    a.flow_hist = reinterpret_cast<int32_t *>(ws + L.flow_hist);
     return a;
 }
 
@@ -1001,12 +1713,20 @@ cudaError_t launch_dpg_only(const fs_code *c, const uint8_t *erased, uint8_t *ws
 
 }  // namespace
 
-// The symbolic pass, then, when the column payload is selected and the code
-// fits it, that payload's plan.
+bool flow_applies(const fs_code *c);
+namespace {
+cudaError_t launch_flow_plan(const fs_code *c, uint8_t *ws, cudaStream_t s);
+}  // namespace
+
+// The symbolic pass, then the plan of the payload that will run: the column
+// payload's when it is selected and the code fits it, else the dataflow
+// walk's where it applies.
 cudaError_t launch_dpg(const fs_code *c, const uint8_t *erased, uint8_t *ws, uint8_t *unrecovered,
                        int32_t *n_unrecovered, cudaStream_t s) {
     cudaError_t e = launch_dpg_only(c, erased, ws, unrecovered, n_unrecovered, s);
     if (e == cudaSuccess && c->peel_columns && col_fits(c)) e = launch_col_plan(c, ws, s);
+    if (e == cudaSuccess && !(c->peel_columns && col_fits(c)) && flow_applies(c))
+        e = launch_flow_plan(c, ws, s);
     return e;
 }
 
@@ -1041,7 +1761,81 @@ PeelArgs peel_args(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_
     a.hints = c->l2_hints;
     a.status = reinterpret_cast<int32_t *>(ws) + WS_STATUS;
     a.L = (int32_t)peel_slice_words(c);
+    a.flow = 0;  // the launcher turns the dataflow walk on where it applies
+    a.k_int = c->k_int;
+    a.fhdr = reinterpret_cast<const int32_t *>(ws + L.flow_hdr);
+    a.funits = reinterpret_cast<const uint2 *>(ws + L.flow_units);
+    a.fbatch = reinterpret_cast<const uint4 *>(ws + L.flow_batch);
+    a.fmem = reinterpret_cast<const uint16_t *>(ws + L.flow_mem);
+    a.fslot = reinterpret_cast<const int32_t *>(ws + L.flow_slot);
     return a;
+}
+
+}  // namespace
+
+// The dataflow walk applies to one 1024-thread CTA per SM, 16-bit block ids
+// and levels, rows of at most kFlowMaxDeg and padded graphs whose offsets fit
+// 20 bits.
+bool flow_applies(const fs_code *c) {
+    return c->peel_flow && c->peel_ctas == 1 && c->k_int <= 65535 && c->n_con <= 65535 &&
+           c->max_con_deg <= kFlowMaxDeg && c->e_con4 < (int64_t)kMoffMask;
+}
+
+namespace {
+
+// Check accumulator slots of the payload: at most kFlowSlots, and at most
+// 64 KiB of shared memory.
+int flow_slot_cap(int64_t L) { return (int)std::min<int64_t>(kFlowSlots, 65536 / (16 * L)); }
+
+size_t flow_smem(const fs_code *c) { return c->smem_optin & ~(size_t)15; }
+
+cudaError_t launch_flow_plan(const fs_code *c, uint8_t *ws, cudaStream_t s) {
+    const DecodeLayout L = decode_layout(c);
+    const int64_t Lw = peel_slice_words(c);
+    const int slots = flow_slot_cap(Lw);
+    const size_t smem = flow_smem(c);
+    FlowUnitArgs u;
+    u.hdr = reinterpret_cast<const int32_t *>(ws);
+    u.pair_rec = reinterpret_cast<const int4 *>(ws + L.pair_rec);
+    u.con_ptr = c->con_ptr;
+    u.con_idx4 = c->con_idx4;
+    u.lvl = reinterpret_cast<const uint16_t *>(ws + L.flow_lvl);
+    u.n = c->n;
+    u.slot_cap = slots;
+    u.fhdr = reinterpret_cast<int32_t *>(ws + L.flow_hdr);
+    u.hist = reinterpret_cast<int32_t *>(ws + L.flow_hist);
+    u.ucnt = reinterpret_cast<int32_t *>(ws + L.flow_ucnt);
+    u.slot_nseg = reinterpret_cast<int32_t *>(ws + L.flow_slot);
+    u.uarea = reinterpret_cast<uint2 *>(ws + L.flow_uarea);
+    u.ukey = reinterpret_cast<uint16_t *>(ws + L.flow_ukey);
+    u.raw = reinterpret_cast<uint16_t *>(ws + L.flow_raw);
+    // a warp for every possible pair; those past the path's pairs return
+    const int ctas = (c->k_int + kFlowUnitThreads / 32 - 1) / (kFlowUnitThreads / 32);
+    k_flow_units<<<std::max(ctas, 1), kFlowUnitThreads, 0, s>>>(u);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    FlowPlaceArgs a;
+    a.hdr = u.hdr;
+    a.hist = u.hist;
+    a.ucnt = u.ucnt;
+    a.pair_rec = u.pair_rec;
+    a.uarea = u.uarea;
+    a.ukey = u.ukey;
+    a.raw = u.raw;
+    a.fhdr = u.fhdr;
+    a.units = reinterpret_cast<uint2 *>(ws + L.flow_units);
+    a.batches = reinterpret_cast<uint4 *>(ws + L.flow_batch);
+    a.mem = reinterpret_cast<uint16_t *>(ws + L.flow_mem);
+    // the payload's shared memory less its ready flags, counters and accumulators
+    const int64_t rest = (int64_t)smem - ((c->k_int + 15) & ~15) - ((4 * slots + 15) & ~15) -
+                         (int64_t)slots * Lw * 16;
+    a.cap_bytes = (int32_t)std::max<int64_t>(rest, 0);
+    a.slot_cap = slots;
+    a.smem_bytes = (int32_t)smem;
+    e = cudaFuncSetAttribute(k_flow_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_flow_place<<<1, 1024, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -1049,17 +1843,23 @@ PeelArgs peel_args(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_
 cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_t *ws,
                         cudaStream_t s) {
     if (c->peel_columns && col_fits(c)) return launch_peel_col(c, coded, data_out, ws, s);
-    const PeelArgs a = peel_args(c, coded, data_out, ws);
+    PeelArgs a = peel_args(c, coded, data_out, ws);
     const int64_t Lw = a.L;
-    const size_t smem = peel_smem_bytes(Lw);
-    cudaError_t e =
-        cudaFuncSetAttribute(k_peel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    size_t smem = peel_smem_bytes(Lw);
+    if (flow_applies(c)) {
+        // all the shared memory the CTA may have: the plan's size depends on
+        // the path, which only the device knows (k_flow_plan checks it)
+        a.flow = 1;
+        smem = std::max(smem, flow_smem(c));
+    }
+    const auto kern = a.flow ? k_peel_flow : k_peel;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // one CTA per SM: 1024 threads; several: the SM's threads split between them
     const int threads =
         c->peel_ctas >= 4 ? kPeelThreads / 4 : (c->peel_ctas >= 2 ? kPeelThreads / 2 : kPeelThreads);
     const int64_t n_slices = (c->tw + Lw - 1) / Lw;
-    k_peel<<<(unsigned)n_slices, threads, smem, s>>>(a);
+    kern<<<(unsigned)n_slices, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@ TUNE_PEEL_CTAS, TUNE_GATHER_CTAS, TUNE_DPG_COMPACT, TUNE_L2_HINTS = 1, 2, 3, 4
 TUNE_ENCODE_SLICES = 5
 TUNE_ROWS_PER_TICKET = 6
 TUNE_PEEL_COLUMNS = 7
+TUNE_PEEL_FLOW = 8
 WS_STATUS_OFFSET = 0
 
 #: every symbol declared in include/founsure_gpu.h

@@ -321,11 +321,11 @@ def test_wide_check_level_splits_into_steps(cols, t):
 
 
 @pytest.mark.parametrize("knob,value", [(1, 2), (1, 4), (2, 1), (3, 0), (4, 1), (5, 0), (5, 2),
-                                        (5, 3), (7, 1)])
+                                        (5, 3), (7, 1), (8, 1)])
 def test_tuning_knobs_leave_results_unchanged(knob, value):
     """Payload CTAs per SM, one gather CTA per SM, general (not compact)
     decoding schedule, L2 eviction hints, row-gather encode, 16- and 32-byte
-    slice encode, column payload."""
+    slice encode, column payload, the barrier-free (dataflow) payload walk."""
     import torch
     fs = _fs()
     case = Case(1500, 60, 2000, 4096 + 32, gen.DIST_FINITE40)
@@ -549,3 +549,49 @@ def test_chained_precode_validation():
         fs.Code(graph([[0, 1], [2, 4], [1, 2]]), 16)  # check 1 reads its own parity
     with pytest.raises(fs.FounsureError):
         fs.Code(graph([[0, 1], [2, 3], [1, 2]]), 16)  # level 1 before level 0
+
+
+@pytest.mark.parametrize("case", ["precoded_joint", "precoded_two_pass", "long_chain", "wide_checks",
+                                  "rsd_plain", "array_precode", "config2"])
+def test_flow_payload_matches_oracle(case):
+    """The barrier-free payload walk (FS_TUNE_PEEL_FLOW = 1), byte for byte
+    against the oracle: precode checks summed in shared-memory slots and
+    heavy rows chained through their output block (precoded, both decoding
+    modes, several erasure rates), one symbol per level, checks of 32
+    members in one level, long RSD rows (units of more than one round of
+    loads), a chained (array) precode whose checks read parities, and the
+    full-size precoded stripe."""
+    fs = _fs()
+    flow = {fs.TUNE_PEEL_FLOW: 1}
+    if case.startswith("precoded"):
+        c = Case(700, 40, 950, 272, gen.DIST_FINITE40, mode=1 if case.endswith("two_pass") else 0)
+        c.code.set_tuning(fs.TUNE_PEEL_FLOW, 1)
+        _, p, cd = c.encode_gpu()
+        _, cod = oracle.encode(c.g, c.data, c.t)
+        for s, frac in enumerate((0.1, 0.2, 0.3)):
+            _check_decode(c, cod, cd, _erased(c.n, frac, gen.SEED_ERASE + (s << 20)))
+    elif case == "long_chain":
+        b = 1100
+        g = _graph_from_rows(b, [[0]] + [[j - 1, j] for j in range(1, b)])
+        assert _check_plain(g, 32, np.zeros(b, np.uint8), flow).n_levels == b
+    elif case == "wide_checks":
+        b, m = 2048, 64
+        g = _graph_from_rows(b, [[v] for v in range(b + m)],
+                             [[j + 64 * i for i in range(32)] for j in range(m)])
+        erased = np.zeros(b + m, np.uint8)
+        erased[:64] = 1
+        assert not _check_plain(g, 4096 + 48, erased, flow).unrecovered.any()
+    elif case == "rsd_plain":
+        g = gen.make_graph(2000, 0, 2600, gen.DIST_RSD, 0.05, 0.01)
+        for s in range(2):
+            _check_plain(g, 1024 + 16, _erased(2600, 0.1, gen.SEED_ERASE + (s << 20)), flow)
+    elif case == "array_precode":
+        # p = 67, two levels of 67 checks (the second reads parities of the first)
+        g = gen.make_graph_array(1005, 1139, 1481, gen.DIST_FINITE40)
+        _check_plain(g, 512, _erased(g.n, 0.15, gen.SEED_ERASE), flow)
+    else:
+        c = Case(4096, 128, 5400, 65536, gen.DIST_FINITE40)
+        c.code.set_tuning(fs.TUNE_PEEL_FLOW, 1)
+        _, p, cd = c.encode_gpu()
+        _, cod = oracle.encode(c.g, c.data, c.t)
+        _check_decode(c, cod, cd, _erased(c.n, 0.2, gen.SEED_ERASE))
