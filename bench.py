@@ -41,12 +41,15 @@ from paper_1702_07409_gb300 import gen  # noqa: E402
 B, M, N_CODED, T = 4096, 128, 5400, 65536
 ERASE_FRAC, UPDATE_FRAC, REPAIR_FRAC = 0.20, 0.01, 0.05
 METRIC = "encode & BP-decode source GB/s"
-# DRAM bytes (read + write) of one launch at this workload, from the ncu
-# captures summarised in profiles/k_peel_precoded_k4096_t64k.md and
-# profiles/k_slices_precoded_k4096_t64k.md (valid while those kernels are
-# unchanged)
-PEEL_TRAFFIC_BYTES = 1039106048 + 278187008
-SLICES_TRAFFIC_BYTES = 273448192 + 313286656
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the payload (k_peel) and of the slice encode (k_slices) at this workload,
+# taken with
+#   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
+#       --clock-control none -k regex:"k_peel|k_slices" -s 6 -c 2
+#       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-extras
+# on one GB300. Valid only while those two kernels are unchanged.
+PEEL_TRAFFIC_BYTES = 1040141824 + 278360320
+SLICES_TRAFFIC_BYTES = 272906752 + 312706304
 WORKLOAD = ("precoded LDGM stripe: b=4096 x 64 KiB data, m=128 checks (3 per data block), "
             "n=5400, FiniteDist max-degree-40, 20% erasures; step = encode + decode + "
             "1% update + 5% repair")
@@ -412,12 +415,111 @@ def run_gpu(args):
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                    "reasons": clocks["reasons"]},
     }
+    if rank == 0 and world == 1 and not args.no_extras:
+        line.update(extras(args, st, device, dec_bytes, peak, peak_kind))
+        del st
+        torch.cuda.empty_cache()
+        line["batched"] = compact_batched(batched_measure(args, device, args.extras_stripes, 5))
+        torch.cuda.empty_cache()
+        line["serving"] = compact_serving(serving_measure(args, device, args.extras_requests))
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_slice, args.cpu_steps)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.cpu_slice, args.cpu_steps)
+        line["levels"] = level_counts(line.get("decode_roofline", {}).get("levels_gpu"))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def extras(args, st, device, dec_bytes, peak, peak_kind):
+    """Numbers beside the step, on one GPU: the decode as a decode-only call
+    pays it (schedule, then payload, serially) against its own roofline, and
+    the latency of the small plain-LT code (k = 100 x 1 KiB, RSD(0.1, 0.05),
+    n = 150, 30 erased), where a launch's latency, not bandwidth, is what a
+    caller sees."""
+    import torch
+    from paper_1702_07409_gb300 import founsure as fs
+    bk = st.bufs[0]
+    K = max(args.steps, 10)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    for i in range(3):
+        st.code.decode_schedule(bk["erased"], bk["unrec"], bk["nun"], st.ws_d)
+        st.code.decode_payload(st.cd, bk["out"], st.ws_d)
+    torch.cuda.synchronize()
+    for i in range(K):
+        ev[i][0].record()
+        st.code.decode_schedule(bk["erased"], bk["unrec"], bk["nun"], st.ws_d)
+        ev[i][1].record()
+        st.code.decode_payload(st.cd, bk["out"], st.ws_d)
+        ev[i][2].record()
+    torch.cuda.synchronize()
+    sch = statistics.median(e[0].elapsed_time(e[1]) for e in ev)
+    pay = statistics.median(e[1].elapsed_time(e[2]) for e in ev)
+    tot = statistics.median(e[0].elapsed_time(e[2]) for e in ev)
+    view = st.code.decode_path(st.ws_d)
+    ach = dec_bytes / (tot * 1e-3) / 1e9
+    out = {"decode_roofline": {
+        "bound": "hbm", "kernel": "k_dpg_compact + k_peel (fs_decode: schedule, then payload)",
+        "ms": round(tot, 4), "schedule_ms": round(sch, 4), "payload_ms": round(pay, 4),
+        "achieved": round(ach, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+        "frac": round(ach / peak, 4), "algorithmic_bytes": dec_bytes,
+        "levels_gpu": int(view["n_levels"])}}
+
+    # config 1: k = 100 x 1 KiB, plain LT, RSD(0.1, 0.05), n = 150, 30 erased
+    b1, n1, t1 = 100, 150, 1024
+    g1 = gen.make_graph(b1, 0, n1, gen.DIST_RSD, 0.1, 0.05)
+    c1 = fs.Code(g1, t1)
+    d1 = torch.from_numpy(gen.fill_bytes(gen.SEED_DATA, b1 * t1).reshape(b1, t1)).to(device)
+    cd1 = torch.empty((n1, t1), dtype=torch.uint8, device=device)
+    er1 = np.zeros(n1, np.uint8)
+    er1[gen.sample_indices(n1, 30, gen.SEED_ERASE)] = 1
+    der1 = torch.from_numpy(er1).to(device)
+    o1 = torch.empty((b1, t1), dtype=torch.uint8, device=device)
+    u1 = torch.empty(b1, dtype=torch.uint8, device=device)
+    nu1 = torch.empty(1, dtype=torch.int32, device=device)
+    we1, wd1 = c1.workspace(fs.OP_ENCODE, device=device), c1.workspace(fs.OP_DECODE, device=device)
+    R = 200
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(R)]
+    for i in range(R + 5):
+        e = evs[i - 5] if i >= 5 else None
+        if e: e[0].record()
+        c1.encode(d1, None, cd1, we1)
+        if e: e[1].record()
+        c1.decode(cd1, der1, o1, u1, nu1, wd1)
+        if e: e[2].record()
+    torch.cuda.synchronize()
+    enc_us = statistics.median(e[0].elapsed_time(e[1]) for e in evs) * 1e3
+    dec_us = statistics.median(e[1].elapsed_time(e[2]) for e in evs) * 1e3
+    out["config1_latency"] = {
+        "workload": "k=100 x 1 KiB, plain LT, RSD(0.1, 0.05), n=150, 30 coded blocks erased",
+        "encode_us": round(enc_us, 2), "decode_us": round(dec_us, 2), "unit": "us",
+        "unrecovered": int(nu1.item()), "calls": R,
+        "note": "one call each, median of %d back-to-back calls on one stream (CUDA events)" % R}
+    c1.close()
+    return out
+
+
+def compact_batched(line):
+    """The batched-stripes line cut to what the step line carries."""
+    return {"stripes": int(line["config"]["workload"].split()[0]),
+            "graph_replay_ms": line["ms_per_step"], "per_stripe_ms": line["per_stripe_ms"],
+            "eager_ms": line["batched_eager_ms"],
+            "speedup_vs_per_stripe": line["speedup_vs_per_stripe"],
+            "source_gbs": line["value"], "achieved": line["roofline"]["achieved"],
+            "frac": line["roofline"]["frac"], "unit": "GB/s",
+            "outputs_equal_per_stripe": line["outputs_equal_per_stripe"],
+            "workload": line["config"]["workload"]}
+
+
+def compact_serving(line):
+    """The serving line cut to what the step line carries."""
+    b, o = line["batched"], line["one_request_per_launch"]
+    keep = ("p50_ms", "p99_ms", "served", "gbs", "waves", "dropped", "rejected")
+    return {"requests": line["steps"], "workload": line["config"]["workload"],
+            "continuous_batching": {k: b.get(k) for k in keep},
+            "one_request_per_launch": {k: o.get(k) for k in keep}}
 
 
 def _oracle_step(g, data, erased, idx, new, lost, t):
@@ -452,6 +554,93 @@ def cpu_baseline(slice_bytes: int, steps: int = 2):
             "sample": "%d steps of the same stripe, graph and erasures on a %d-byte slice of "
                       "every block (full block 65536 B)" % (steps, t),
             "seconds": round(dt, 2)}
+
+
+def _oracle_proc(slice_bytes, steps, seed_off, q, go):
+    """One process of the all-cores baseline: the unchanged oracle on its own
+    byte slice of every block (its data drawn from seed + seed_off); it
+    starts when every process is ready (go)."""
+    import oracle
+    g = gen.make_graph(B, M, N_CODED, gen.DIST_FINITE40)
+    t = slice_bytes
+    data = gen.fill_bytes(gen.SEED_DATA + seed_off, B * t).reshape(B, t)
+    er = np.zeros(N_CODED, np.uint8)
+    er[gen.sample_indices(N_CODED, gen.round_count(ERASE_FRAC, N_CODED), gen.SEED_ERASE)] = 1
+    u, nl = gen.round_count(UPDATE_FRAC, B), gen.round_count(REPAIR_FRAC, N_CODED)
+    q.put(("ready", 0, 0.0))
+    go.wait(600)
+    src = 0
+    t0 = time.perf_counter()
+    for r in range(steps):
+        idx = gen.sample_indices(B, u, gen.SEED_UPDATE + (r << gen.ROUND_SHIFT))
+        new = gen.fill_bytes(gen.SEED_NEWDATA + (r << gen.ROUND_SHIFT), u * t).reshape(u, t)
+        lost = gen.sample_indices(N_CODED, nl, gen.SEED_REPAIR + (r << gen.ROUND_SHIFT))
+        out, path, data = _oracle_step(g, data, er, idx, new, lost, t)
+        src += B * t + int((path.unrecovered[:B] == 0).sum()) * t
+    q.put(("done", src, time.perf_counter() - t0))
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def cpu_baseline_all_cores(slice_bytes: int, steps: int):
+    """The oracle, unchanged, in one process per host core, each on its own
+    byte slice of every block of the same stripe (Section 3.1's parallel
+    scheme: every byte slice is an independent copy of the same problem).
+    Processes are spawned (not forked: this process holds a CUDA context)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    q, go = ctx.Queue(), ctx.Event()
+    per = max(1, steps // 2)
+    procs = [ctx.Process(target=_oracle_proc, args=(slice_bytes, per, p, q, go)) for p in range(n)]
+    for pr in procs:
+        pr.start()
+    for _ in range(n):
+        assert q.get(timeout=600)[0] == "ready"
+    t0 = time.perf_counter()
+    go.set()
+    done = [q.get(timeout=600) for _ in range(n)]
+    wall = time.perf_counter() - t0
+    for pr in procs:
+        pr.join(timeout=600)
+    src = sum(x[1] for x in done)
+    return {"value": round(src / wall / 1e9, 4), "unit": "GB/s", "cores": n, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": "%d processes, each %d steps of the same stripe, graph and erasures on its "
+                      "own %d-byte slice of every block (distinct seeded bytes per process)"
+                      % (n, per, slice_bytes),
+            "seconds": round(wall, 2)}
+
+
+def level_counts(levels_gpu):
+    """Algorithm 5's level count (the delayed schedule, which the GPU runs)
+    beside Algorithm 1's count of sweeps with immediate updates (t_m of
+    Section 3.1), both from the oracle on the stripe's erasure draw."""
+    import oracle
+    g = gen.make_graph(B, M, N_CODED, gen.DIST_FINITE40)
+    er = np.zeros(N_CODED, np.uint8)
+    er[gen.sample_indices(N_CODED, gen.round_count(ERASE_FRAC, N_CODED), gen.SEED_ERASE)] = 1
+    path = oracle.dpg(g, er)
+    order = np.arange(N_CODED + M, dtype=np.int32)
+    unrec, sweeps = oracle.peel_immediate(g, er, order, with_sweeps=True)
+    return {"algorithm5_delayed_levels": int(path.n_levels), "gpu_levels": levels_gpu,
+            "algorithm1_immediate_sweeps": int(sweeps),
+            "same_recovered_set": bool(np.array_equal(unrec, path.unrecovered)),
+            "note": "Algorithm 1 visits the constraints in index order (coded rows, then checks)"}
 
 
 def run_reference(args):
@@ -500,25 +689,36 @@ def run_reference(args):
 
 
 def run_batched(args):
-    """Many uneven stripes (plain LT, RSD(0.05, 0.01) degrees): k uniform in
-    [64, 4096], t from {4, 16, 64} KiB, n = round(1.3 k), 10-25% of each
-    stripe's coded blocks erased. One step = encode + decode of every stripe.
-    Compares one CUDA-graph replay of the batch (fs_batch: a fixed number of
-    launches), the same batch run eagerly, and per-stripe fs_encode +
-    fs_decode calls; the batched outputs are checked against the per-stripe
-    ones byte for byte."""
+    """The batched-stripes workload as its own JSON line (see batched_measure)."""
     import torch
-    from paper_1702_07409_gb300 import autotune
-    from paper_1702_07409_gb300 import founsure as fs
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
+    line = batched_measure(args, device, args.stripes, args.steps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def batched_measure(args, device, S, K):
+    """Many uneven stripes (plain LT, RSD(0.05, 0.01) degrees): k uniform in
+    [64, 4096], t from {4, 16, 64} KiB, n = round(1.3 k), 10-25% of each
+    stripe's coded blocks erased. One step = encode + decode of every stripe.
+    Compares one CUDA-graph replay of the batch (fs_batch: a fixed number of
+    launches), the same batch run eagerly, and per-stripe fs_encode +
+    fs_decode calls; the batched outputs are checked against the per-stripe
+    ones byte for byte. Returns the JSON line (a dict)."""
+    import torch
+    from paper_1702_07409_gb300 import autotune
+    from paper_1702_07409_gb300 import founsure as fs
+    rank, world, local = dist_env()
     peak, peak_kind = peaks()
     rng = np.random.default_rng(gen.SEED_GRAPH + rank)
-    S = args.stripes
     ks = rng.integers(64, 4097, S)
     ts = rng.choice([4096, 16384, 65536], S)
     fr = rng.uniform(0.10, 0.25, S)
@@ -601,7 +801,6 @@ def run_batched(args):
         barrier()
         return reduce_max(e0.elapsed_time(e1), device) / K
 
-    K = args.steps
     with ClockSampler(local) as clk:
         ms_graph = timed(graph.replay, K)
     ms_eager = timed(lambda: (enc.run(), dec.run()), K)
@@ -630,11 +829,12 @@ def run_batched(args):
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                    "reasons": clocks["reasons"]},
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    enc.close()
+    dec.close()
+    for s_ in st:
+        s_["code"].close()
+    del st, enc, dec, graph, ref
+    return line
 
 
 def run_repair_local(args):
@@ -953,21 +1153,31 @@ def run_array(args):
 
 
 def run_serving(args):
-    """Requests served from device-resident stripes (paper_1702_07409_gb300.serve):
-    Poisson arrivals (mean 2000 requests/s, seeded exponential gaps) of encode
-    60% / decode 25% / update 10% / repair 5%; stripe sizes log-uniform in
-    [1, 256] MiB rounded to powers of two (so codes are reused), t = 16 or 64
-    KiB, n = 1.3 k, RSD(0.05, 0.01); decodes erase 10-25% of the target's coded
-    blocks, updates rewrite 1% of its data blocks, repairs recompute 5% of its
-    coded blocks; decode / update / repair pick a resident stripe at random
-    from a pre-populated pool; admission under a 120 GB budget. Continuous
-    batching is compared with one request per launch on the same stream of
-    requests."""
+    """The serving workload as its own JSON line (see serving_measure)."""
     import torch
-    from paper_1702_07409_gb300.serve import Request, Server, latency_stats
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
+    line = serving_measure(args, device, args.requests)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serving_measure(args, device, n_requests):
+    """Requests served from device-resident stripes (paper_1702_07409_gb300.serve):
+    Poisson arrivals (mean 2000 requests/s, seeded exponential gaps) of encode
+    60% / decode 25% / update 10% / repair 5%; stripe sizes log-uniform in
+    [1, 256] MiB over the powers of two (each of the 9 sizes equally likely,
+    so codes are reused), t = 16 or 64 KiB, n = 1.3 k, RSD(0.05, 0.01);
+    decodes erase 10-25% of the target's coded blocks, updates rewrite 1% of
+    its data blocks, repairs recompute 5% of its coded blocks; decode /
+    update / repair pick a resident stripe at random from a pre-populated
+    pool; admission under a 120 GB budget. Continuous batching is compared
+    with one request per launch on the same stream of requests. Returns the
+    JSON line (a dict)."""
+    import torch
+    from paper_1702_07409_gb300.serve import Request, Server, latency_stats
+    rank, world, local = dist_env()
     budget = int(args.budget_gb * 1e9)
     sizes = [1 << (20 + j) for j in range(9)]  # 1 MiB .. 256 MiB
 
@@ -981,7 +1191,7 @@ def run_serving(args):
             t_now += float(rng.exponential(1.0 / args.rate))
             u = rng.random()
             if u < 0.60:
-                size = sizes[int(np.clip(np.round(rng.uniform(0, 8)), 0, 8))]
+                size = sizes[int(rng.integers(0, 9))]  # log-uniform over the 9 sizes
                 t = int(rng.choice([16384, 65536]))
                 reqs.append(Request(i, "encode", t_now, k=size // t, t=t, target=sid, seed=10**6 + i))
                 meta[sid] = (size // t, int(round(1.3 * (size // t))))
@@ -1015,7 +1225,7 @@ def run_serving(args):
             t = int(prng.choice([16384, 65536]))
             srv.add_resident(p, size // t, t, seed=500 + p)
             meta[p] = (size // t, srv.stripes[p].n)
-        reqs = draw(args.requests, meta)
+        reqs = draw(n_requests, meta)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         reqs = srv.run(reqs, realtime=True)
@@ -1043,19 +1253,19 @@ def run_serving(args):
     clocks = clk.summary()
     line = {
         "metric": "served source GB/s, p50/p99 latency", "value": batched["gbs"], "unit": "GB/s",
-        "n_gpus": world, "steps": args.requests, "warmup": 0, "ms_per_step": None,
+        "n_gpus": world, "steps": n_requests, "warmup": 0, "ms_per_step": None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded device random bytes, splitmix64 graphs, Poisson arrivals)",
         "config": {"workload": "serving: Poisson %g requests/s, encode 60 / decode 25 / update 10 / "
-                               "repair 5 %%, stripes 1-256 MiB (powers of two), t 16 or 64 KiB, "
-                               "n = 1.3 k, budget %g GB, pool %d" % (args.rate, args.budget_gb, args.pool),
-                   "requests": args.requests},
+                               "repair 5 %%, stripes 1-256 MiB (the 9 powers of two equally likely), "
+                               "t 16 or 64 KiB, n = 1.3 k, budget %g GB, pool %d"
+                               % (args.rate, args.budget_gb, args.pool),
+                   "requests": n_requests},
         "batched": batched, "one_request_per_launch": single,
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                    "reasons": clocks["reasons"]},
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -1069,6 +1279,13 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=12,
                     help="steps of the oracle in cpu_baseline (about 0.85 s each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the decode-only, config-1, batched and serving numbers of the "
+                         "default line")
+    ap.add_argument("--extras-stripes", type=int, default=512,
+                    help="stripes of the batched object in the default line")
+    ap.add_argument("--extras-requests", type=int, default=600,
+                    help="requests of the serving object in the default line")
     ap.add_argument("--l2-hints", action="store_true",
                     help="tuning knob: L2 evict-last / evict-first hints")
     ap.add_argument("--peel-flow", action="store_true",
