@@ -347,7 +347,8 @@ fs_status fs_repair(const fs_code *code, const int32_t *d_lost, int32_t n_lost, 
  *             or FS_ERR_TIMEOUT if a bounded wait gave up); NULL to skip
  * Returns FS_ERR_SCRATCH when fs_workspace_bytes(code, FS_OP_ENCODE, 0)
  * exceeds FS_ENCODE_STATIC_SCRATCH_BYTES (the encode of this library needs
- * only its status word, so every code fits today), FS_ERR_INVALID for bad
+ * only its status word and the work-ticket counters of its launches, 256
+ * bytes whatever the block size, so every code fits today), FS_ERR_INVALID for bad
  * arguments or when the current device is not the
  * code's device. It calls no allocator. The first call on each device looks
  * up the area's device address (make it before any stream capture). All

@@ -22,6 +22,8 @@ SHAPES = [
     (90, 0, 117, 16384, gen.DIST_RSD, 0.05, 0.01),
     (512, 16, 700, 256, gen.DIST_FINITE40, 0.0, 0.0),
     (4096, 0, 5325, 1024, gen.DIST_RSD, 0.05, 0.01),  # slice tables in several parts
+    (512, 0, 666, 65536, gen.DIST_RSD, 0.05, 0.01),    # a 64 KiB stripe (config 3 draws t up to it)
+    (300, 12, 400, 65536, gen.DIST_FINITE40, 0.0, 0.0),
 ]
 
 

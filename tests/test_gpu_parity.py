@@ -152,6 +152,51 @@ def test_update_and_repair_rounds():
         assert np.array_equal(_host(cd), cod)
 
 
+def test_config4_full_size_rounds():
+    """Config 4 at its own size: the precoded stripe (b=4096 x 64 KiB, m=128,
+    n=5400) through 10 rounds of 1% of the data rewritten (41 blocks) and 5%
+    of the coded blocks lost and repaired (270). Every round, every block is
+    compared with the oracle on two sampled byte slices (byte slices are
+    independent copies of the same problem, so the oracle encodes only those
+    columns); at full width the delta-updated parities and coded blocks must
+    equal a fresh encode of the updated data, and the repaired blocks the
+    bytes they had before the loss."""
+    import torch
+    b, m, n, t = 4096, 128, 5400, 65536
+    case = Case(b, m, n, t, gen.DIST_FINITE40)
+    d, p, cd = case.encode_gpu()
+    cols = np.r_[0:4096, t // 2 + 1024:t // 2 + 3072]  # two slices, 6 KiB of every block
+    ts = cols.size
+    data_s = case.data[:, cols].copy()
+    u, nl = gen.round_count(0.01, b), gen.round_count(0.05, n)
+    ws_u = case.code.workspace(_fs().OP_UPDATE, u)
+    ws_r = case.code.workspace(_fs().OP_REPAIR)
+    ws_e = case.code.workspace(_fs().OP_ENCODE)
+    dcols = torch.from_numpy(cols).cuda()
+    p2 = torch.empty_like(p)
+    cd2 = torch.empty_like(cd)
+    for rnd in range(10):
+        idx = gen.sample_indices(b, u, gen.SEED_UPDATE + (rnd << gen.ROUND_SHIFT))
+        new = gen.fill_bytes(gen.SEED_NEWDATA + (rnd << gen.ROUND_SHIFT), u * t).reshape(u, t)
+        case.code.update(_dev(idx), u, _dev(new), d, p, cd, ws_u)
+        data_s, par_s, cod_s = oracle.update(case.g, data_s, idx, new[:, cols], ts)
+        assert case.code.ws_status(ws_u) == 0
+        assert np.array_equal(_host(d.index_select(1, dcols)), data_s)
+        assert np.array_equal(_host(p.index_select(1, dcols)), par_s)
+        assert np.array_equal(_host(cd.index_select(1, dcols)), cod_s)
+        case.code.encode(d, p2, cd2, ws_e)
+        assert torch.equal(p2, p) and torch.equal(cd2, cd)
+        lost = gen.sample_indices(n, nl, gen.SEED_REPAIR + (rnd << gen.ROUND_SHIFT))
+        dl = torch.from_numpy(lost).long().cuda()
+        before = cd.index_select(0, dl)
+        cd.index_fill_(0, dl, 0)
+        case.code.repair(_dev(lost), nl, d, p, cd, ws_r)
+        assert case.code.ws_status(ws_r) == 0
+        assert torch.equal(cd.index_select(0, dl), before)
+        assert np.array_equal(_host(cd.index_select(0, dl).index_select(1, dcols)),
+                              oracle.repair(case.g, data_s, lost, ts))
+
+
 def test_encode_rows_and_empty_calls():
     import torch
     case = Case(300, 12, 420, 64, gen.DIST_FINITE40)

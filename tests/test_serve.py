@@ -118,3 +118,70 @@ def test_budget_eviction_rejection_and_cancel():
     torch.cuda.synchronize()
     assert srv.peak <= srv.budget
     srv.close()
+
+
+def test_served_results_match_the_oracle():
+    """Every result of a mixed, continuously batched run against the oracle:
+    the run is replayed on the host stripe by stripe in arrival order (the
+    order the server keeps for each stripe), each decode's bytes and
+    unrecovered count are compared, and each stripe's final data and coded
+    bytes are compared after its updates and repairs. The inputs are the
+    server's own seeded draws: graphs from its code rule, erasures, indices
+    and lost rows from the generator, bytes from the same seeded torch
+    generator."""
+    import torch
+    import oracle
+    from paper_1702_07409_gb300 import gen
+    from paper_1702_07409_gb300.serve import Server
+    srv = Server(1 << 30, streams=3, batching=True)
+    shapes = list(zip([32, 64, 128, 300, 64, 32], [64, 1024, 4096, 64, 4096, 1024]))
+    for i, (k, t) in enumerate(shapes):
+        srv.add_resident(i, k=k, t=t, seed=10 + i)
+    reqs = srv.run(_requests(), realtime=False)
+    torch.cuda.synchronize()
+
+    def seeded_bytes(seed, rows, cols):
+        g = torch.Generator(device="cuda")
+        g.manual_seed(seed)
+        return torch.randint(0, 256, (rows, cols), dtype=torch.uint8, device="cuda",
+                             generator=g).cpu().numpy()
+
+    def graph(k, t):
+        n = int(round(k / srv.rate))
+        return gen.make_graph(k, 0, n, gen.DIST_RSD, 0.05, 0.01, stripe=(k * 131 + t) & 0xFFF)
+
+    state = {}
+    for i, (k, t) in enumerate(shapes):
+        g = graph(k, t)
+        d = seeded_bytes(10 + i, k, t)
+        state[i] = [g, t, d, oracle.encode(g, d, t)[1]]
+    checked = {"decode": 0, "update": 0, "repair": 0, "encode": 0}
+    for r in sorted(reqs, key=lambda q: (q.arrival, q.rid)):
+        if r.out.get("dropped") or r.out.get("rejected"):
+            continue
+        checked[r.kind] += 1
+        if r.kind == "encode":
+            g = graph(r.k, r.t)
+            d = seeded_bytes(r.seed, r.k, r.t)
+            state[r.target] = [g, r.t, d, oracle.encode(g, d, r.t)[1]]
+            continue
+        g, t, d, c = state[r.target]
+        if r.kind == "decode":
+            er = np.zeros(g.n, np.uint8)
+            er[gen.sample_indices(g.n, gen.round_count(r.erase_frac, g.n), r.seed)] = 1
+            want, path = oracle.decode(g, c, er, t)
+            assert np.array_equal(r.out["data_out"].cpu().numpy(), want)
+            assert int(r.out["n_unrecovered"].item()) == int(path.unrecovered.sum())
+        elif r.kind == "update":
+            idx = gen.sample_indices(g.b, r.n_update, r.seed)
+            d, _, c = oracle.update(g, d, idx, seeded_bytes(r.seed, r.n_update, t), t)
+            state[r.target] = [g, t, d, c]
+        else:  # a repair puts back exactly the stored bytes of the lost rows
+            lost = gen.sample_indices(g.n, r.n_lost, r.seed)
+            assert np.array_equal(oracle.repair(g, d, lost, t), c[lost])
+    assert all(v > 0 for v in checked.values()), checked
+    for sid, st in srv.stripes.items():
+        g, t, d, c = state[sid]
+        assert np.array_equal(st.data.cpu().numpy(), d)
+        assert np.array_equal(st.coded.cpu().numpy(), c)
+    srv.close()

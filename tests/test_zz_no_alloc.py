@@ -54,8 +54,47 @@ def test_static_encode_matches_encode_twice_in_a_row():
 
 def test_static_encode_area_covers_large_blocks():
     """The static area holds the encode workspace of large-block codes too:
-    the host check that would refuse a code beyond it lets them through."""
+    the host check that would refuse a code beyond it lets them through, and
+    a precoded code of 16 MiB blocks encodes through the static area exactly
+    as through fs_encode."""
+    import torch
     from paper_1702_07409_gb300 import founsure as fs
     g = gen.make_graph(8, 0, 12, gen.DIST_RSD, 0.1, 0.05)
     code = fs.Code(g, 256 * 1024 * 1024)  # 256 MiB blocks; nothing is allocated for them
     assert code.workspace_bytes(fs.OP_ENCODE) <= fs.ENCODE_STATIC_SCRATCH_BYTES
+    code.close()
+    g = gen.make_graph(12, 3, 18, gen.DIST_FINITE40)
+    (p0, c0), (p1, c1), status, code = _encode_both(fs, g, 16 * 1024 * 1024, 9)
+    assert status == fs.FS_OK
+    assert torch.equal(c1, c0) and torch.equal(p1, p0)
+    code.close()
+
+
+def test_static_encode_rejects_bad_pointers():
+    """Host-side checks, before anything is enqueued: a null data or coded
+    pointer, a missing parity buffer for a precoded code, and a buffer not on
+    a 16-byte boundary each return FS_ERR_INVALID."""
+    import torch
+    from paper_1702_07409_gb300 import founsure as fs
+    g = gen.make_graph(60, 4, 90, gen.DIST_FINITE40)
+    t = 1024
+    code = fs.Code(g, t)
+    data = torch.zeros((g.b * t + 16,), dtype=torch.uint8, device="cuda")
+    par = torch.empty((g.m * t + 16,), dtype=torch.uint8, device="cuda")
+    cod = torch.empty((g.n * t + 16,), dtype=torch.uint8, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    vp = ctypes.c_void_p
+
+    def call(d, p, c):
+        return fs.lib().fs_encode_static(code._h, d, p, c, None, stream)
+
+    d, p, c = vp(data.data_ptr()), vp(par.data_ptr()), vp(cod.data_ptr())
+    assert call(None, p, c) == fs.FS_ERR_INVALID
+    assert call(d, p, None) == fs.FS_ERR_INVALID
+    assert call(d, None, c) == fs.FS_ERR_INVALID            # the code has parities
+    assert call(vp(data.data_ptr() + 1), p, c) == fs.FS_ERR_INVALID
+    assert call(d, p, vp(cod.data_ptr() + 8)) == fs.FS_ERR_INVALID
+    torch.cuda.synchronize()
+    assert call(d, p, c) == fs.FS_OK                         # the same buffers, aligned
+    torch.cuda.synchronize()
+    code.close()
