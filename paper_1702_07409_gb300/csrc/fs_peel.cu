@@ -254,6 +254,209 @@ __device__ __forceinline__ void advance(LevelCursor &cur, int nt, const int4 &le
     ++cur.level;
 }
 
+// Exclusive prefix sum of one counter over the first nw warps of the block
+// (the warps holding items), like warps_excl_scan4; *total receives the sum.
+// Consecutive calls alternate buf.
+__device__ int warps_excl_scan1(int x, int *total, int (*s_warp)[32], int buf, int nw) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (nw == 1) {
+        *total = __shfl_sync(0xffffffffu, v, 31);
+        return v - x;
+    }
+    if (lane == 31) s_warp[buf][wid] = v;
+    asm volatile("bar.sync 1, %0;\n" ::"r"(nw * 32) : "memory");
+    const int t = lane < nw ? s_warp[buf][lane] : 0;
+    int b = lane < wid ? t : 0, all = t;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        all += __shfl_xor_sync(0xffffffffu, all, o);
+    }
+    *total = all;
+    return b + v - x;
+}
+
+// Step B of a level in the compact form: only what the next levels need.
+// The level's pairs go out as pair_f / pair_g and a record stub {f, g,
+// level, 0} (format_path turns the stubs into the payload's records after
+// the walk), f's level for the dataflow plan, and the level-relative offset
+// of f's adjacency slots into lvl_v for step C (lvl_v[nt] = the level's
+// total, also in *s_tot: read it after the next block barrier). Called by
+// every thread; only the warps holding pairs scan.
+template <typename PairOf>
+__device__ void emit_pairs(const DpgArgs &a, LevelCursor &cur, int nt, PairOf pair_of, int32_t *lvl_v,
+                           int (*s_warp1)[32], int *s_tot) {
+    int len = 0;
+    for (int base = 0; base < nt; base += blockDim.x) {
+        const int nw = (min(nt - base, (int)blockDim.x) + 31) >> 5;  // warps holding pairs
+        const int buf = cur.scan_buf;
+        cur.scan_buf ^= 1;
+        if ((int)(threadIdx.x >> 5) >= nw) continue;
+        const int i = base + threadIdx.x;
+        int32_t vdeg = 0;
+        if (i < nt) {
+            int32_t f, g;
+            pair_of(i, &f, &g, &vdeg);
+            const int32_t p = cur.np + i;
+            a.pair_f[p] = f;
+            a.pair_g[p] = g;
+            a.pair_rec[2 * (size_t)p] = make_int4(f, g, cur.level, 0);
+            a.flow_lvl[f] = (uint16_t)cur.level;
+        }
+        int total;
+        const int off = warps_excl_scan1(vdeg, &total, s_warp1, buf, nw);
+        if (i < nt) lvl_v[i] = len + off;
+        len += total;
+    }
+    if (threadIdx.x == 0) {  // warp 0 holds pairs whenever nt > 0
+        a.level_off[cur.level] = cur.np;
+        lvl_v[nt] = len;
+        *s_tot = len;
+    }
+}
+
+// Block-wide exclusive scan of two counters (x, y); *tot receives the sums.
+// Every thread calls it; s_w holds 32 int2 of scratch.
+__device__ int2 block_excl_scan2(int2 c, int2 *tot, int2 *s_w) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    int2 v = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, v.x, o);
+        const int b = __shfl_up_sync(0xffffffffu, v.y, o);
+        if (lane >= o) {
+            v.x += a;
+            v.y += b;
+        }
+    }
+    if (lane == 31) s_w[wid] = v;
+    __syncthreads();
+    int2 before = make_int2(0, 0), all = make_int2(0, 0);
+    for (int j = 0; j < nw; ++j) {
+        const int2 t = s_w[j];
+        if (j < wid) {
+            before.x += t.x;
+            before.y += t.y;
+        }
+        all.x += t.x;
+        all.y += t.y;
+    }
+    __syncthreads();
+    *tot = all;
+    return make_int2(before.x + v.x - c.x, before.y + v.y - c.y);
+}
+
+// After the walk of the compact form: the payload's records from the pair
+// list (levels are contiguous ranges of pairs, so the level-relative offsets
+// are differences of prefix sums over the whole list). Per pair x = padded
+// row length (its recipe), y = its segments of kRecipeSeg entries, z = 1 when
+// it has several (a multi-segment pair takes an accumulator). Writes
+// pair_rec, seg_pair, chunk_pair and level_tab exactly as emit_level does
+// level by level, and fills cur's totals and maxima for finish_dpg. The
+// workspace's front_a / front_b / touched arrays (unused by this form, each
+// at least n_con + 1 >= levels + 1 entries) hold each level's prefixes.
+__device__ void format_path(const DpgArgs &a, LevelCursor &cur, const int32_t *cptr4, int2 *s_w2,
+                            int *s_max) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int32_t P = cur.np, NL = cur.level;
+    auto sizes = [&](int32_t g, int *x, int *y, int *z) {
+        *x = cptr4[g + 1] - cptr4[g];
+        *y = (*x + kRecipeSeg - 1) / kRecipeSeg;
+        *z = *y > 1 ? 1 : 0;
+    };
+    if (tid < 4) s_max[tid] = 0;
+    // A: prefixes in pair order, kept in pair_rec[2p + 1] until C
+    const int per = (P + T - 1) / T;
+    const int p0 = min(P, tid * per), p1 = min(P, p0 + per);
+    int2 cxy = make_int2(0, 0);
+    int cz = 0;
+    for (int32_t p = p0; p < p1; ++p) {
+        int x, y, z;
+        sizes(a.pair_rec[2 * (size_t)p].y, &x, &y, &z);
+        cxy.x += x;
+        cxy.y += y;
+        cz += z;
+    }
+    int2 txy, tz2;
+    int2 oxy = block_excl_scan2(cxy, &txy, s_w2);
+    int2 oz = block_excl_scan2(make_int2(cz, 0), &tz2, s_w2);
+    for (int32_t p = p0; p < p1; ++p) {
+        const int4 r = a.pair_rec[2 * (size_t)p];
+        int x, y, z;
+        sizes(r.y, &x, &y, &z);
+        a.pair_rec[2 * (size_t)p + 1] = make_int4(oxy.x, oxy.y, oz.x, r.z);
+        oxy.x += x;
+        oxy.y += y;
+        oz.x += z;
+    }
+    __syncthreads();
+    // B: per level its first pair's prefixes, its totals, and its segment
+    // and chunk list bases (each level's lists start on multiples of 4)
+    const int perl = (NL + T - 1) / T;
+    const int l0 = min(NL, tid * perl), l1 = min(NL, l0 + perl);
+    int2 c4 = make_int2(0, 0);
+    for (int32_t l = l0; l < l1; ++l) {
+        const int32_t first = a.level_off[l], next = l + 1 < NL ? a.level_off[l + 1] : P;
+        const int4 gf = a.pair_rec[2 * (size_t)first + 1];
+        const int4 gn = next < P ? a.pair_rec[2 * (size_t)next + 1] : make_int4(txy.x, txy.y, tz2.x, 0);
+        const int recipes = gn.x - gf.x, segs = gn.y - gf.y, multi = gn.z - gf.z;
+        a.front_a[l] = gf.x;
+        a.front_b[l] = gf.y;
+        a.touched[l] = gf.z;
+        c4.x += (segs + 3) & ~3;
+        c4.y += ((recipes >> 2) + 3) & ~3;
+        atomicMax(s_max + 0, next - first);
+        atomicMax(s_max + 1, recipes);
+        atomicMax(s_max + 2, segs);
+        atomicMax(s_max + 3, multi);
+    }
+    int2 t4;
+    int2 base = block_excl_scan2(c4, &t4, s_w2);
+    for (int32_t l = l0; l < l1; ++l) {
+        const int32_t first = a.level_off[l], next = l + 1 < NL ? a.level_off[l + 1] : P;
+        const int4 gf = a.pair_rec[2 * (size_t)first + 1];
+        const int4 gn = next < P ? a.pair_rec[2 * (size_t)next + 1] : make_int4(txy.x, txy.y, tz2.x, 0);
+        const int recipes = gn.x - gf.x, segs = gn.y - gf.y;
+        a.level_tab[2 * l] = make_int4(first, next - first, base.x, segs);
+        a.level_tab[2 * l + 1] = make_int4(base.y, recipes >> 2, 0, 0);
+        base.x += (segs + 3) & ~3;
+        base.y += ((recipes >> 2) + 3) & ~3;
+    }
+    __syncthreads();
+    // C: the records and the segment / chunk lists
+    for (int32_t p = p0; p < p1; ++p) {
+        const int4 r = a.pair_rec[2 * (size_t)p];
+        const int4 gp = a.pair_rec[2 * (size_t)p + 1];
+        const int32_t l = r.z, first = a.level_off[l], i = p - first;
+        int x, y, z;
+        sizes(r.y, &x, &y, &z);
+        const int ro = gp.x - a.front_a[l], so = gp.y - a.front_b[l];
+        const int mslot = z ? gp.z - a.touched[l] : -1;
+        const int4 lt0 = a.level_tab[2 * l], lt1 = a.level_tab[2 * l + 1];
+        a.pair_rec[2 * (size_t)p] = make_int4(r.x, r.y, ro, mslot);
+        a.pair_rec[2 * (size_t)p + 1] = make_int4(cptr4[r.y], x, so, y);
+        for (int k = 0; k < y; ++k) a.seg_pair[lt0.z + so + k] = i;
+        for (int k = 0; k < (x >> 2); ++k) a.chunk_pair[lt1.x + (ro >> 2) + k] = i;
+    }
+    if (tid == 0) {
+        cur.sb = t4.x;
+        cur.cb = t4.y;
+    }
+    __syncthreads();
+    cur.maxp = s_max[0];
+    cur.maxr = s_max[1];
+    cur.maxs = s_max[2];
+    cur.maxm = s_max[3];
+    cur.sb = t4.x;
+    cur.cb = t4.y;
+}
+
 // End of the pass: totals, the staged flag, unrecovered flags and list.
 __device__ void finish_dpg(const DpgArgs &a, const LevelCursor &cur, const uint8_t *known,
                            int *s_cnt, int *s_cnt_data) {
@@ -472,8 +675,9 @@ __device__ __forceinline__ void red_add_shared(uint32_t *p, uint32_t v) {
 
 __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgCompactPlace &pl) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int4 s_warp4[2][32];
-    __shared__ int4 s_len;
+    __shared__ int s_warp1[2][32];
+    __shared__ int2 s_w2[32];
+    __shared__ int s_tot, s_max[4];
     // symbols of the next level, by level parity (a level reads one list
     // while its step C2 fills the other)
     __shared__ int s_nt[2], s_cnt, s_cnt_data;
@@ -541,15 +745,16 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
             __syncthreads();
             continue;
         }
-        // B: pairs of the level (adjacency slots into lvl_v for step C)
-        emit_level(
+        // B: pairs of the level (adjacency slots into lvl_v for step C); their
+        // records for the payload are formatted after the walk
+        emit_pairs(
             a, cur, nt,
             [&](int i, int32_t *f, int32_t *g, int32_t *vdeg) {
                 *f = touched[i];
                 *g = (int32_t)(best[*f] & 0xffffu);
                 *vdeg = vptr[*f + 1] - vptr[*f];
             },
-            cptr4, lvl_v, s_warp4, &s_len);
+            lvl_v, s_warp1, &s_tot);
         for (int i = tid; i < nt; i += T) {
             const int32_t f = touched[i];
             best[f] = kE;
@@ -557,7 +762,7 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
         }
         if (tid == 0) s_nt[par ^ 1] = 0;  // the list the next level's bids fill
         __syncthreads();
-        const int4 len = s_len;
+        const int4 len = make_int4(0, 0, 0, s_tot);  // adjacency slots of the level
         const bool mapped = len.w <= kSlotCap;  // uniform: slots of each pair listed
         if (mapped) {
             for (int i = tid; i < nt; i += T) {
@@ -595,8 +800,10 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
                 claim_and_bid(c, par ^ 1);
         }
         __syncthreads();
-        advance(cur, nt, len);
+        cur.np += nt;
+        ++cur.level;
     }
+    format_path(a, cur, cptr4, s_w2, s_max);
     finish_dpg(a, cur, known, &s_cnt, &s_cnt_data);
 }
 
