@@ -42,14 +42,25 @@ B, M, N_CODED, T = 4096, 128, 5400, 65536
 ERASE_FRAC, UPDATE_FRAC, REPAIR_FRAC = 0.20, 0.01, 0.05
 METRIC = "encode & BP-decode source GB/s"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the payload (k_peel) and of the slice encode (k_slices) at this workload,
-# taken with
+# the payload (k_peel_keys, the default key walk) and of the slice encode
+# (k_slices) at this workload, taken with
 #   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
-#       --clock-control none -k regex:"k_peel|k_slices" -s 6 -c 2
+#       --clock-control none -k regex:"k_peel|k_slices|k_key_plan" -s 9 -c 3
 #       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-extras
 # on one GB300. Valid only while those two kernels are unchanged.
-PEEL_TRAFFIC_BYTES = 1040141824 + 278360320
-SLICES_TRAFFIC_BYTES = 272906752 + 312706304
+PEEL_TRAFFIC_BYTES = 645942272 + 311390720
+SLICES_TRAFFIC_BYTES = 273567232 + 310150912
+# the payload's walk (FS_TUNE_PEEL_FLOW; the library's default is 2): its
+# kernel, and the plan kernels the decoding schedule adds for it
+PEEL_KERNEL = {0: "k_peel", 1: "k_peel_flow", 2: "k_peel_keys"}
+PLAN_KERNELS = {0: [], 1: ["k_flow_units", "k_flow_place"], 2: ["k_key_plan"]}
+DEFAULT_WALK = 2
+
+
+def walk_of(args):
+    return DEFAULT_WALK if getattr(args, "peel_flow", None) is None else args.peel_flow
+
+
 WORKLOAD = ("precoded LDGM stripe: b=4096 x 64 KiB data, m=128 checks (3 per data block), "
             "n=5400, FiniteDist max-degree-40, 20% erasures; step = encode + decode + "
             "1% update + 5% repair")
@@ -201,8 +212,9 @@ class Stripe:
         self.host_nun = torch.empty(1, dtype=torch.int32).pin_memory()
         self.nun_reads = []
 
-    # launches of this library's kernels per step (encode 1: the slice
-    # kernel; decode 2: schedule + payload; update 4; repair 1)
+    # launches of this library's kernels per step, besides the decoding
+    # plan's (encode 1: the slice kernel; decode 2: schedule + payload;
+    # update 4; repair 1)
     LAUNCHES_PER_STEP = 8
 
     @property
@@ -307,8 +319,8 @@ def run_gpu(args):
         tuning[fs.TUNE_GATHER_CTAS] = args.gather_ctas
     if args.l2_hints:
         tuning[fs.TUNE_L2_HINTS] = 1
-    if args.peel_flow:
-        tuning[fs.TUNE_PEEL_FLOW] = 1
+    if args.peel_flow is not None:
+        tuning[fs.TUNE_PEEL_FLOW] = args.peel_flow
 
     st = Stripe(rank, max(args.steps, 1) + args.warmup, device, tuning,
                 overlap=not args.serial_schedule, two_pass=args.two_pass)
@@ -363,7 +375,7 @@ def run_gpu(args):
     gbs_e2e = world * src_bytes / (ms_e2e * 1e-3) / 1e9
 
     # roofline of the kernel with the largest share of the step: the payload
-    # peel (k_peel). Algorithmic bytes = the coded payloads of the pairs whose
+    # (k_peel_keys by default). Algorithmic bytes = the coded payloads of the pairs whose
     # constraint is a coded row (read) + the recovered data blocks (written).
     g = st.g
     dec_pairs_lt = None
@@ -391,15 +403,16 @@ def run_gpu(args):
                    "schedule_beside_encode": not args.serial_schedule,
                    "decoding": "two-pass (LT, then precode)" if args.two_pass else "joint",
                    "tuning": {"peel_ctas": args.peel_ctas or 1,
-                              "gather_ctas": args.gather_ctas or 8}},
+                              "gather_ctas": args.gather_ctas or 8,
+                              "peel_flow": walk_of(args)}},
         "ops_ms": {k: round(v, 4) for k, v in op_ms.items()},
         "encode_source_gbs": round(B * T / (op_ms["encode"] * 1e-3) / 1e9, 1),
         "decode_source_gbs": round(recovered / ((op_ms["decode_schedule"] +
                                                   op_ms["decode_payload"]) * 1e-3) / 1e9, 1),
-        "roofline": {"bound": "hbm", "kernel": "k_peel (fs_decode_payload)",
+        "roofline": {"bound": "hbm", "kernel": f"{PEEL_KERNEL[walk_of(args)]} (fs_decode_payload)",
                      "achieved": round(dec_gbs, 1), "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s", "frac": round(dec_gbs / peak, 4),
-                     "traffic": PEEL_TRAFFIC_BYTES if T == 65536 else None,
+                     "traffic": PEEL_TRAFFIC_BYTES if T == 65536 and walk_of(args) == DEFAULT_WALK else None,
                      "algorithmic_bytes": dec_bytes},
         "encode_roofline": {"bound": "hbm", "kernel": "k_slices (fs_encode)",
                             "achieved": round(enc_gbs, 1), "peak": peak, "unit": "GB/s",
@@ -411,7 +424,7 @@ def run_gpu(args):
                 "copies": "uploads and read-backs on two copy streams, overlapping the "
                           "neighbouring steps' kernels (two input sets)",
                 "readback_verified": e2e_ok},
-        "gpu_launches": Stripe.LAUNCHES_PER_STEP * K,
+        "gpu_launches": (Stripe.LAUNCHES_PER_STEP + len(PLAN_KERNELS[walk_of(args)])) * K,
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                    "reasons": clocks["reasons"]},
     }
@@ -461,7 +474,9 @@ def extras(args, st, device, dec_bytes, peak, peak_kind):
     view = st.code.decode_path(st.ws_d)
     ach = dec_bytes / (tot * 1e-3) / 1e9
     out = {"decode_roofline": {
-        "bound": "hbm", "kernel": "k_dpg_compact + k_peel (fs_decode: schedule, then payload)",
+        "bound": "hbm",
+        "kernel": " + ".join(["k_dpg_compact"] + PLAN_KERNELS[walk_of(args)] + [PEEL_KERNEL[walk_of(args)]]) +
+                  " (fs_decode: schedule, then payload)",
         "ms": round(tot, 4), "schedule_ms": round(sch, 4), "payload_ms": round(pay, 4),
         "achieved": round(ach, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
         "frac": round(ach / peak, 4), "algorithmic_bytes": dec_bytes,
@@ -1053,6 +1068,8 @@ def run_array(args):
     n, m = (13 * k + 5) // 10, k - b
     g = gen.make_graph_array(b, k, n, gen.DIST_FINITE40)
     code = fs.Code(g, T)
+    if args.peel_flow is not None:
+        code.set_tuning(fs.TUNE_PEEL_FLOW, args.peel_flow)
     gen_t = torch.Generator(device=device)
     gen_t.manual_seed(gen.SEED_DATA + rank)
     data = torch.randint(0, 256, (b, T), dtype=torch.uint8, device=device, generator=gen_t)
@@ -1132,7 +1149,7 @@ def run_array(args):
                    "l2": "inputs larger than L2 (no flush)"},
         "ops_ms": {"encode": round(enc_ms, 4), "decode_schedule": round(sch_ms, 4),
                    "decode_payload": round(pay_ms, 4)},
-        "roofline": {"bound": "hbm", "kernel": "k_peel (fs_decode_payload)",
+        "roofline": {"bound": "hbm", "kernel": f"{PEEL_KERNEL[walk_of(args)]} (fs_decode_payload)",
                      "achieved": round(pay_bytes / (pay_ms * 1e-3) / 1e9, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(pay_bytes / (pay_ms * 1e-3) / 1e9 / peak, 4), "traffic": None,
@@ -1291,9 +1308,9 @@ def main():
                     help="requests of the serving object in the default line")
     ap.add_argument("--l2-hints", action="store_true",
                     help="tuning knob: L2 evict-last / evict-first hints")
-    ap.add_argument("--peel-flow", action="store_true",
-                    help="tuning knob: the payload walks the path without level barriers "
-                         "(fewer HBM bytes, more instructions)")
+    ap.add_argument("--peel-flow", type=int, choices=[0, 1, 2], default=None,
+                    help="tuning knob FS_TUNE_PEEL_FLOW: 0 the level walk, 1 the dataflow walk "
+                         "without level barriers, 2 the key walk (default: the library's)")
     ap.add_argument("--two-pass", action="store_true",
                     help="decode in the paper's two passes (LT code, then the precode) "
                          "instead of jointly")

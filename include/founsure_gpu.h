@@ -145,25 +145,32 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
  *                        by the decoding schedule: set the knob before
  *                        fs_decode / fs_decode_schedule (a payload without
  *                        the plan reports FS_ERR_INVALID in the workspace)
- *   FS_TUNE_PEEL_FLOW    1: the slice payload walks the decoding path
- *                        without a barrier between levels, on a plan made
- *                        by the decoding schedule: a heavy decoder (more
- *                        than 8 loads: precode checks, high-degree rows)
- *                        is gathered in pieces, each as soon as its members
- *                        exist, while L2 still holds them, and small
- *                        gathers are packed into full rounds of 8 loads;
- *                        each gather waits only for the blocks it reads.
- *                        It reads fewer bytes from HBM (at 4096 x 64 KiB,
- *                        n = 5400, 20% erased: 0.60 GB against 1.04 GB)
- *                        but issues more instructions and its plan costs a
- *                        second one-CTA pass, so it is not the default. It
- *                        applies to codes of at most 65535 intermediates and
- *                        constraints, rows of at most 4000 entries and
- *                        FS_TUNE_PEEL_CTAS = 1, and to paths whose plan fits
- *                        shared memory; elsewhere the payload walks level by
- *                        level. Set it before fs_decode / fs_decode_schedule
- *                        (the schedule makes the plan). 0 (default): level
- *                        by level
+ *   FS_TUNE_PEEL_FLOW    how the slice payload walks the decoding path.
+ *                        2 (default), the key walk: a heavy decoder (more
+ *                        than 8 loads: precode checks, high-degree rows) is
+ *                        gathered in pieces of 8 of its members, in the
+ *                        order the schedule recovered them; each piece runs
+ *                        right after the level that produced its last member
+ *                        (while L2 still holds its members) and adds to a
+ *                        partial sum kept in the output block; every other
+ *                        pair is one gather at its own level; one barrier
+ *                        per level. The schedule records the member order
+ *                        and a one-CTA plan kernel lays the gathers out
+ *                        (about 25 us at 4096 x 64 KiB, n = 5400, 20%
+ *                        erased, where the payload reads 0.65 GB from HBM
+ *                        against 1.04 GB level by level and runs 12%
+ *                        faster). 1: the same pieces without level
+ *                        barriers, each gather waiting only for the blocks it
+ *                        reads (fewer HBM bytes still, more instructions:
+ *                        slower). 0: level by level, every pair whole.
+ *                        Walks 1 and 2 apply to codes of at most 65535
+ *                        intermediates and constraints, rows of at most
+ *                        4000 entries, FS_TUNE_PEEL_CTAS = 1 and the compact
+ *                        schedule (walk 2), and to paths whose plan fits
+ *                        the plan kernel's tables and the payload's stages
+ *                        (at most 1024 levels); elsewhere the payload walks
+ *                        level by level. Set it before fs_decode /
+ *                        fs_decode_schedule (the schedule makes the plan)
  * Returns FS_ERR_INVALID for an unknown knob or an out-of-range value. Not
  * thread-safe against concurrent hot calls on the same code. */
 #define FS_TUNE_PEEL_CTAS   1
@@ -238,7 +245,11 @@ fs_status fs_decode_payload(const fs_code *code, const void *d_coded, void *d_da
  * the decoding path DP of Algorithm 5 as pairs (pair_f[p], pair_g[p]) for
  * p < *n_pairs, level l owning pairs [level_off[l], level_off[l+1]) for
  * l < *n_levels. Inside a level the pair order is unspecified. Constraint g
- * is coded row g for g < n and precode check g - n otherwise. */
+ * is coded row g for g < n and precode check g - n otherwise. plan is the
+ * header of the payload plan that FS_TUNE_PEEL_FLOW makes: {units, loads,
+ * 1 when the plan was made, check slots, batches, checks seen, 1 when a pair
+ * had too many segments, 1 when the plan suits the key walk} (all zero
+ * when the knob is 0 or the code does not fit the plan). */
 typedef struct {
     const int32_t *n_levels;  /* device int32 */
     const int32_t *n_pairs;   /* device int32 */
@@ -246,6 +257,7 @@ typedef struct {
     const int32_t *pair_f;    /* device int32[k_int] */
     const int32_t *pair_g;    /* device int32[k_int] */
     const uint8_t *parity;    /* device [m*t]: recovered parity intermediates */
+    const int32_t *plan;      /* device int32[8]: the payload plan's header */
 } fs_path_view;
 fs_status fs_decode_path(const fs_code *code, const void *d_ws, fs_path_view *out);
 
@@ -308,8 +320,8 @@ fs_status fs_repair_local(const fs_local *local, const uint8_t *d_lost, void *d_
                           size_t block_bytes, uint8_t *d_unrepaired, int32_t *d_n_unrepaired,
                           void *d_ws, void *stream);
 /* The repair path of the last fs_repair_local on d_ws, as device views: pair
- * (f, g) = coded block f from group g, levels as in fs_decode_path; parity is
- * NULL. */
+ * (f, g) = coded block f from group g, levels as in fs_decode_path; parity and
+ * plan are NULL. */
 fs_status fs_local_path(const fs_local *local, const void *d_ws, fs_path_view *out);
 
 /*

@@ -197,7 +197,7 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     c->encode_slices = 1;
     c->rows_per_ticket = 16;
     c->peel_columns = 0;
-    c->peel_flow = 0;
+    c->peel_flow = 2;
     cudaError_t e = cudaGetDevice(&c->device);
     int v = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c->device);
@@ -271,7 +271,7 @@ FS_API fs_status fs_code_set_tuning(fs_code *c, int knob, int value) {
             c->peel_columns = value;
             return FS_OK;
         case FS_TUNE_PEEL_FLOW:
-            if (value != 0 && value != 1) return FS_ERR_INVALID;
+            if (value < 0 || value > 2) return FS_ERR_INVALID;
             c->peel_flow = value;
             return FS_OK;
     }
@@ -379,6 +379,7 @@ FS_API fs_status fs_decode_path(const fs_code *c, const void *d_ws, fs_path_view
     out->pair_f = reinterpret_cast<const int32_t *>(w + L.pair_f);
     out->pair_g = reinterpret_cast<const int32_t *>(w + L.pair_g);
     out->parity = w + L.parity;
+    out->plan = reinterpret_cast<const int32_t *>(w + L.flow_hdr);
     return FS_OK;
 }
 

@@ -68,7 +68,8 @@ struct fs_code {
     int rows_per_ticket;  // coded rows per work ticket of the row-gather encode (1..16)
     int peel_columns;     // 1: column payload (every intermediate of a byte column in
                           // shared memory) when the code fits it; 0 (default): slice payload
-    int peel_flow;        // 1: the slice payload walks the path without level barriers
+    int peel_flow;        // 2 (default): the key walk; 1: the dataflow walk without
+                          // level barriers; 0: the level walk
                           // where its plan fits; 0 (default): level by level
     // slice encode tables (present when sl_slots > 0): every input block has
     // a 16-byte shared-memory slot per byte slice; data block v is slot v,
@@ -187,14 +188,25 @@ enum {
 // packs them into batches of at most 8 loads (flow_batch, 16 bytes each; at
 // most one per unit) and lays their loads out in that order (flow_mem):
 //   flow_hdr[0..7] = {units, loads, ok, check slots used, batches, slot
-//                     counter, overflow, 0}
+//                     counter, overflow, key walk fits}
 //   flow_slot[s]   = segments of the check that sums into accumulator s
+// The key walk's plan (FS_TUNE_PEEL_FLOW = 2, one CTA: k_key_plan) has the
+// same units and loads, every heavy pair chained, without batches. The
+// compact schedule records, for every constraint of degree >= kListDeg, its
+// members in the order it recovered them (ascending level) at the
+// constraint's padded row offset (flow_list, 16 bits each) and, for every
+// pair p, its level | the degree of its constraint << 16 (flow_pinfo); units of key k
+// (whole pairs, then chain links) and their loads fill one range each:
+//   flow_ktab[2k..2k+1] = key k: {first unit, units, first unit rounded down
+//                     to even, units from there rounded up to even}, {first
+//                     load rounded down to a multiple of 8, loads from there
+//                     rounded up to one, 0, 0}
 constexpr int kFlowSlots = 128;  // check accumulator slots of the dataflow payload
 struct DecodeLayout {
     size_t res, xs, best, known, front_a, front_b, touched, pair_f, pair_g, pair_rec, level_off,
         level_tab, seg_pair, chunk_pair, unrec_list, parity, col_src, col_step, col_seg, flow_hdr,
         flow_lvl, flow_hist, flow_ucnt, flow_uarea, flow_ukey, flow_raw, flow_units, flow_batch,
-        flow_mem, flow_slot, total;
+        flow_mem, flow_slot, flow_ktab, flow_list, flow_pinfo, total;
     int64_t col_max_segs, col_max_steps, flow_max_units, flow_max_loads;
 };
 
@@ -240,6 +252,9 @@ static inline DecodeLayout decode_layout(const fs_code *c) {
     L.flow_batch = o; o = fs_align256(o + 16 * (size_t)L.flow_max_units + 16);  // uint4 records
     L.flow_mem = o;   o = fs_align256(o + 2 * (size_t)L.flow_max_loads + 16);
     L.flow_slot = o;  o = fs_align256(o + 4 * (size_t)kFlowSlots);
+    L.flow_ktab = o;  o = fs_align256(o + 32 * (K + 2));  // keys: at most levels + 1
+    L.flow_list = o;  o = fs_align256(o + 2 * (size_t)c->e_con4 + 16);
+    L.flow_pinfo = o; o = fs_align256(o + 4 * (K + 1));
     L.total = o;
     return L;
 }

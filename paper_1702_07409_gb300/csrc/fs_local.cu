@@ -631,5 +631,6 @@ FS_API fs_status fs_local_path(const fs_local *o, const void *d_ws, fs_path_view
     out->pair_f = reinterpret_cast<const int32_t *>(w + L.pair_f);
     out->pair_g = reinterpret_cast<const int32_t *>(w + L.pair_g);
     out->parity = nullptr;
+    out->plan = nullptr;
     return FS_OK;
 }

@@ -150,6 +150,18 @@ __device__ __forceinline__ T *place(unsigned char *smem, int32_t off, T *global)
 // ---------------------------------------------------------------------------
 // symbolic pass
 
+}  // namespace
+
+bool flow_applies(const fs_code *c);
+
+namespace {
+
+// flow_hdr word set to 1 by the compact schedule when it wrote flow_list
+constexpr int kFlowHdrList = 8;
+// constraints whose members the compact schedule lists in recovery order:
+// those a pair of which can have more than 8 loads (kFlowSeg)
+constexpr int kListDeg = 9;
+
 struct DpgArgs {
     const int32_t *con_ptr, *con_ptr4, *con_xs, *var_ptr, *var_idx;
     const uint8_t *erased;
@@ -170,6 +182,11 @@ struct DpgArgs {
     int32_t *flow_hdr;
     uint16_t *flow_lvl;
     int32_t *flow_hist;
+    // the key walk's plan: members of every constraint of degree >=
+    // kListDeg in the order they were recovered, and every pair's level and
+    // constraint degree; or null
+    uint16_t *flow_list;
+    uint32_t *flow_pinfo;
 };
 
 // stage: -1 joint (every surviving coded row and every check), 0 coded rows
@@ -362,7 +379,7 @@ __device__ int2 block_excl_scan2(int2 c, int2 *tot, int2 *s_w) {
 // workspace's front_a / front_b / touched arrays (unused by this form, each
 // at least n_con + 1 >= levels + 1 entries) hold each level's prefixes.
 __device__ void format_path(const DpgArgs &a, LevelCursor &cur, const int32_t *cptr4, int2 *s_w2,
-                            int *s_max) {
+                            int *s_max, const uint16_t *deg) {
     const int tid = threadIdx.x, T = blockDim.x;
     const int32_t P = cur.np, NL = cur.level;
     auto sizes = [&](int32_t g, int *x, int *y, int *z) {
@@ -443,6 +460,7 @@ __device__ void format_path(const DpgArgs &a, LevelCursor &cur, const int32_t *c
         a.pair_rec[2 * (size_t)p + 1] = make_int4(cptr4[r.y], x, so, y);
         for (int k = 0; k < y; ++k) a.seg_pair[lt0.z + so + k] = i;
         for (int k = 0; k < (x >> 2); ++k) a.chunk_pair[lt1.x + (ro >> 2) + k] = i;
+        if (a.flow_pinfo) a.flow_pinfo[p] = (uint32_t)l | ((uint32_t)deg[r.y] << 16);
     }
     if (tid == 0) {
         cur.sb = t4.x;
@@ -489,7 +507,7 @@ __device__ void finish_dpg(const DpgArgs &a, const LevelCursor &cur, const uint8
         *a.n_unrecovered = *s_cnt;
         a.hdr[WS_N_UNREC_DATA] = *s_cnt_data;
         a.hdr[WS_COL_STEPS] = -1;  // no column payload plan for this path (yet)
-        for (int i = 0; i < 8; ++i) a.flow_hdr[i] = 0;  // ... and no dataflow plan
+        for (int i = 0; i <= kFlowHdrList; ++i) a.flow_hdr[i] = 0;  // ... and no dataflow plan
     }
 }
 
@@ -780,7 +798,13 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
             const int32_t f = touched[i];
             const int32_t c = vidx[vptr[f] + (u - lvl_v[i])];
             red_xor_shared(pk + c, (uint32_t)f);
-            red_add_shared(pk + c, 0xffff0000u);  // -(1 << 16): decrement res
+            if (a.flow_list && deg[c] >= kListDeg) {
+                // f is the (deg - res)-th member of c to be recovered
+                const uint32_t old = atomicAdd(pk + c, 0xffff0000u);
+                a.flow_list[cptr4[c] + (int)deg[c] - (int)((old >> 16) & 0x7fffu)] = (uint16_t)f;
+            } else {
+                red_add_shared(pk + c, 0xffff0000u);  // -(1 << 16): decrement res
+            }
             if (mapped) slots[u] = (uint16_t)c;
         }
         __syncthreads();
@@ -803,8 +827,9 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
         cur.np += nt;
         ++cur.level;
     }
-    format_path(a, cur, cptr4, s_w2, s_max);
+    format_path(a, cur, cptr4, s_w2, s_max, deg);
     finish_dpg(a, cur, known, &s_cnt, &s_cnt_data);
+    if (tid == 0 && a.flow_list) a.flow_hdr[kFlowHdrList] = 1;  // after finish_dpg's clear
 }
 
 __global__ void __launch_bounds__(kDpgThreads, 1) k_dpg_compact(DpgArgs a, DpgCompactPlace pl) {
@@ -864,13 +889,15 @@ struct PeelArgs {
     int32_t L;  // words of every block per CTA
     int32_t hints;  // 1: gathered / recovered blocks evict-last, coded payloads evict-first
     int32_t *status;
-    // dataflow walk (flow_body): on when 1, on the plan of k_flow_plan
+    // dataflow walk (flow_body) when 1, key walk (keys_body) when 2, on the
+    // plan of k_flow_units / k_flow_place
     int32_t flow;
     int32_t k_int;
     const int32_t *fhdr, *fslot;
     const uint2 *funits;
     const uint4 *fbatch;
     const uint16_t *fmem;
+    const int4 *fktab;  // the key walk's table (keys_body)
 };
 
 __device__ __forceinline__ void xor4(uint4 &a, const uint4 &b) {
@@ -1061,6 +1088,13 @@ __device__ __forceinline__ void peel_body(const PeelArgs &a, int64_t slice) {
         // walk at its first level); every thread reads s_ok only after the
         // barrier that follows thread 0's write
         int fail = (threadIdx.x == 0 && !s_ok) ? 1 : 0;
+        // every thread keeps one word k of the slice and takes segments srow,
+        // srow + nrows, ... of each level (no division per item); counted from
+        // the highest thread, so the lowest blockDim.x mod lanes threads take
+        // none and the staging below (thread 0's bulk copies, the low
+        // threads' row copies) overlaps the gathers
+        const int rt0 = (int)blockDim.x - 1 - (int)threadIdx.x;
+        const int k = rt0 % lanes, srow = rt0 / lanes, nrows = (int)blockDim.x / lanes;
         for (int32_t l = 0; l < nl; ++l) {
             const int ps = l % 3, rslot = l & 1;
             // level l's pairs (bulk) and rows (this thread's copies) are in;
@@ -1099,12 +1133,8 @@ __device__ __forceinline__ void peel_body(const PeelArgs &a, int64_t slice) {
             cp_async_commit();
             const int ns = ltab[2 * l].w;
             const uint64_t pol_last = l2_policy_last(), pol_first = l2_policy_first();
-            // every (segment, word): one gather of at most kRecipeSeg blocks;
-            // items go to the highest threads first, so the staging above (thread
-            // 0's bulk copies, the low threads' row copies) overlaps them
-            const int rt = (int)blockDim.x - 1 - (int)threadIdx.x;
-            for (int it = rt; it < ns * lanes; it += blockDim.x) {
-                const int s = it / lanes, k = it - s * lanes;
+            // every (segment, word): one gather of at most kRecipeSeg blocks
+            for (int s = (srow < nrows ? srow : ns); s < ns; s += nrows) {
                 const int32_t *rec = pc + (size_t)sp[s] * kRec;
                 const int32_t f = rec[0], g = rec[1], slot = rec[3];
                 const int sidx = s - rec[6];
@@ -1210,7 +1240,12 @@ enum { kUnitWhole = 0, kUnitSlot = 1, kUnitChain = 2 };
 constexpr uint32_t kMoffMask = (1u << 20) - 1;
 constexpr uint8_t kReadyFinal = 0x80;  // ready flag: x_f is final; low bits: chain segments done
 enum { kFhUnits = 0, kFhLoads = 1, kFhOk = 2, kFhSlots = 3, kFhBatches = 4, kFhSlotCtr = 5,
-       kFhOverflow = 6 };
+       kFhOverflow = 6, kFhKeyFit = 7 };
+// the key walk's shared-memory stages (one key each): units (from an even
+// index) and loads (from a multiple of 8), and the key table
+constexpr int kKeyUnits = 4096;
+constexpr int kKeyMem = 8192;
+constexpr int kKeyMax = 1024;  // 176 KiB of stages in all
 
 // Loads of a unit: c_g, the chain's partial sum, its members; a unit with
 // none (a check of no members decoding its parity: the zero block) keeps one
@@ -1580,6 +1615,316 @@ __global__ void __launch_bounds__(1024, 1) k_flow_place(FlowPlaceArgs a) {
     }
 }
 
+// The key walk's plan: one CTA (it runs beside the encode on the one SM the
+// encode leaves free, right after the schedule), every counter in shared
+// memory. From the path's pairs, the level of every recovered intermediate
+// (flow_lvl) and every heavy constraint's members in the order the schedule
+// recovered them, that is by ascending level (flow_list):
+//   A. a light pair (at most kFlowSeg loads) is one whole unit keyed by its
+//      level; a heavy pair is listed for B;
+//   B. a heavy pair's loads (c_g, then its members in that order) are cut
+//      into segments of S; a segment's key is 1 + the level of its last
+//      member (its highest); runs of equal keys are merged into chain links
+//      (link r > 0 also loads x_f);
+//   C. prefix sums over keys give each key's range of units and loads;
+//   D. every unit and its loads are placed in its key's range: whole pairs
+//      from the front, chain links from the back (the links then run in the
+//      key's last rounds, which measured faster than any mix).
+// A path that does not fit (more keys, heavy pairs or segments than the
+// tables, a key larger than the payload's stages), or whose schedule kept
+// no member order, gets no plan: the header stays zero and the payload walks
+// level by level.
+constexpr int kPlanThreads = 1024;
+constexpr int kPlanHeavy = 1024;  // heavy pairs
+constexpr int kPlanSegs = 4096;   // their segments
+constexpr int kPlanUnits = 8192;  // units, staged in shared memory
+constexpr int kPlanMem = 40960;   // loads, staged in shared memory
+
+struct KeyPlanArgs {
+    const int32_t *hdr;
+    const int4 *pair_rec;
+    const int32_t *con_idx4;
+    const uint16_t *lvl, *list;
+    const uint32_t *pinfo;
+    int32_t n;
+    int32_t *fhdr;
+    int4 *ktab;
+    uint2 *units;
+    uint16_t *mem;
+};
+
+size_t key_plan_smem() {
+    auto up16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    return up16((size_t)6 * 4 * (kKeyMax + 1)) + up16((size_t)kPlanHeavy * (16 + 8)) +
+           up16((size_t)kPlanSegs * (4 + 2)) + up16((size_t)kPlanUnits * 8) + up16((size_t)kPlanMem * 2);
+}
+
+// S (loads per segment) of a heavy pair of `loads` loads: 8, or more when a
+// chain would have more than kFlowChain links.
+__device__ __forceinline__ int plan_seg(int loads) {
+    return max(kFlowSeg, (loads + kFlowChain - 1) / kFlowChain);
+}
+
+// Five pairs of one thread (p0, p0 + T, ...): records, degrees and levels
+// (from flow_pinfo: reads of consecutive words, not scattered ones), all
+// loads in flight together.
+struct PlanPairs {
+    int4 r0[5];
+    int32_t e4[5], deg[5];
+    int lv[5];
+};
+
+__device__ __forceinline__ void plan_pairs(const KeyPlanArgs &a, int32_t p0, int32_t P, int T, PlanPairs &q) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int32_t p = p0 + i * T;
+        if (p < P) {
+            q.r0[i] = __ldg(&a.pair_rec[2 * (size_t)p]);
+            q.e4[i] = __ldg(&a.pair_rec[2 * (size_t)p + 1].x);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const int32_t p = p0 + i * T;
+        if (p < P) {
+            const uint32_t w = a.pinfo[p];
+            q.deg[i] = (int32_t)(w >> 16);
+            q.lv[i] = (int)(w & 0xffffu);
+        }
+    }
+}
+
+// Whether segment j (of the heavy pair whose segments x = {first, count}
+// holds) starts a chain link; if so, the link's last segment *e (relative to
+// the pair) and its index *r among the pair's links (the key changes before
+// it).
+__device__ __forceinline__ bool plan_link(const uint32_t *segk, int2 x, int j, int *e, int *r) {
+    const int s = j - x.x;
+    if (s > 0 && segk[j - 1] == segk[j]) return false;  // not the first segment of its run
+    int ee = s;
+    while (ee + 1 < x.y && segk[x.x + ee + 1] == segk[j]) ++ee;
+    int rr = 0;
+    for (int t = 1; t <= s; ++t) rr += segk[x.x + t] != segk[x.x + t - 1] ? 1 : 0;
+    *e = ee;
+    *r = rr;
+    return true;
+}
+
+__global__ void __launch_bounds__(kPlanThreads, 1) k_key_plan(KeyPlanArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_w[32];
+    __shared__ int s_nh, s_ns, s_bad, s_u, s_m;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int32_t P = a.hdr[WS_N_PAIRS], NL = a.hdr[WS_N_LEVELS];
+    const int nk = NL + 1;
+    if (nk > kKeyMax || a.fhdr[kFlowHdrList] != 1) return;  // no plan (every thread)
+    auto up16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    int *hu = reinterpret_cast<int *>(smem);  // units per key
+    int *hl = hu + (kKeyMax + 1);             // loads per key
+    int *cu = hl + (kKeyMax + 1);             // units placed (whole pairs low 16 bits, links high 16)
+    int *cl = cu + (kKeyMax + 1);             // loads placed
+    int *bu = cl + (kKeyMax + 1);             // first unit
+    int *bl = bu + (kKeyMax + 1);             // first load
+    size_t o = up16((size_t)6 * 4 * (kKeyMax + 1));
+    int4 *hrec = reinterpret_cast<int4 *>(smem + o);  // heavy pair: {f, g, e4, deg}
+    int2 *hx = reinterpret_cast<int2 *>(hrec + kPlanHeavy);  // {first segment, segments}
+    o += up16((size_t)kPlanHeavy * (16 + 8));
+    uint32_t *segk = reinterpret_cast<uint32_t *>(smem + o);  // segment keys
+    uint16_t *segh = reinterpret_cast<uint16_t *>(segk + kPlanSegs);  // segment: its heavy pair
+    o += up16((size_t)kPlanSegs * (4 + 2));
+    // the units and their loads, built here and written out in 16-byte
+    // pieces at the end (scattered 2- and 8-byte stores to global memory
+    // were the plan's largest cost)
+    uint2 *sunit = reinterpret_cast<uint2 *>(smem + o);
+    o += up16((size_t)kPlanUnits * 8);
+    uint16_t *smm = reinterpret_cast<uint16_t *>(smem + o);
+    for (int i = tid; i < 4 * (kKeyMax + 1); i += T) hu[i] = 0;  // hu, hl, cu, cl
+    if (tid == 0) {
+        s_nh = 0;
+        s_ns = 0;
+        s_bad = 0;
+    }
+    __syncthreads();
+
+    // A: five pairs a thread at a time (their loads in flight together)
+    for (int32_t p0 = tid; p0 < P; p0 += 5 * T) {
+        PlanPairs q;
+        plan_pairs(a, p0, P, T, q);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            if (p0 + i * T >= P) continue;
+            const int32_t g = q.r0[i].y, deg = q.deg[i];
+            const int hasg = g < a.n ? 1 : 0, loads = hasg + deg - 1;
+            if (loads <= kFlowSeg) {
+                const int k = min(q.lv[i], (int)NL);
+                atomicAdd(hu + k, 1);
+                atomicAdd(hl + k, max(loads, 1));
+            } else {
+                const int S = plan_seg(loads), nseg = (loads + S - 1) / S;
+                const int h = atomicAdd(&s_nh, 1);
+                const int sg = atomicAdd(&s_ns, nseg);
+                if (h >= kPlanHeavy || sg + nseg > kPlanSegs || deg < kListDeg) {
+                    s_bad = 1;
+                    continue;
+                }
+                hrec[h] = make_int4(q.r0[i].x, g, q.e4[i], deg);
+                hx[h] = make_int2(sg, nseg);
+                for (int j = 0; j < nseg; ++j) segh[sg + j] = (uint16_t)h;
+            }
+        }
+    }
+    __syncthreads();
+    if (s_bad) return;  // no plan (every thread)
+    const int NH = s_nh, NS = s_ns;
+
+    // B: segment keys, one thread a segment: the level of the segment's last
+    // member (its highest: the members come by ascending level) + 1
+    for (int j0 = tid; j0 < NS; j0 += 4 * T) {
+        uint16_t m4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int j = j0 + i * T;
+            m4[i] = 0;
+            if (j < NS) {
+                const int h = segh[j];
+                const int4 hr = hrec[h];
+                const int hasg = hr.y < a.n ? 1 : 0, loads = hasg + hr.w - 1;
+                const int s = j - hx[h].x;
+                m4[i] = a.list[hr.z + min(loads, (s + 1) * plan_seg(loads)) - 1 - hasg];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int j = j0 + i * T;
+            if (j < NS) segk[j] = (uint32_t)min((int)a.lvl[m4[i]] + 1, (int)NL);
+        }
+    }
+    __syncthreads();
+    // ... and the chain links (runs of equal keys) counted per key
+    for (int j = tid; j < NS; j += T) {
+        const int h = segh[j];
+        const int2 x = hx[h];
+        int e, r;
+        if (!plan_link(segk, x, j, &e, &r)) continue;
+        const int4 hr = hrec[h];
+        const int hasg = hr.y < a.n ? 1 : 0, loads = hasg + hr.w - 1;
+        const int S = plan_seg(loads);
+        const int s0 = (j - x.x) * S, s1 = min(loads, (e + 1) * S);
+        atomicAdd(hu + segk[j], 1);
+        atomicAdd(hl + segk[j], (s1 - s0) + (r > 0 ? 1 : 0));
+    }
+    __syncthreads();
+
+    // C: the keys' ranges
+    {
+        const int c0 = tid < nk ? hu[tid] : 0, c1 = tid < nk ? hl[tid] : 0;
+        int U, M;
+        const int ub = flow_block_scan(c0, &U, s_w);
+        const int lb = flow_block_scan(c1, &M, s_w);
+        if (tid < nk) {
+            bu[tid] = ub;
+            bl[tid] = lb;
+            const int u0 = ub & ~1, u1 = (ub + c0 + 1) & ~1, m0 = lb & ~7, m1 = (lb + c1 + 7) & ~7;
+            a.ktab[2 * tid] = make_int4(ub, c0, u0, u1 - u0);
+            a.ktab[2 * tid + 1] = make_int4(m0, m1 - m0, 0, 0);
+            if (u1 - u0 > kKeyUnits || m1 - m0 > kKeyMem) s_bad = 1;
+        }
+        if (tid == 0) {
+            if (M > (int)kMoffMask || M > kPlanMem || U > kPlanUnits) s_bad = 1;
+            s_u = U;
+            s_m = M;
+        }
+        __syncthreads();
+        if (s_bad) return;  // no plan (every thread)
+        if (tid == 0) {
+            a.fhdr[kFhUnits] = U;
+            a.fhdr[kFhLoads] = M;
+        }
+    }
+
+    // D: whole pairs from the front of their key's range ...
+    for (int32_t p0 = tid; p0 < P; p0 += 5 * T) {
+        PlanPairs q;
+        plan_pairs(a, p0, P, T, q);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            if (p0 + i * T >= P) continue;
+            const int32_t f = q.r0[i].x, g = q.r0[i].y, deg = q.deg[i];
+            const int hasg = g < a.n ? 1 : 0, loads = hasg + deg - 1;
+            if (loads > kFlowSeg) continue;
+            const int k = min(q.lv[i], (int)NL);
+            const int pos = bu[k] + (atomicAdd(cu + k, 1) & 0xffff);
+            const int lpos = bl[k] + atomicAdd(cl + k, max(loads, 1));
+            const int4 *row = reinterpret_cast<const int4 *>(a.con_idx4 + q.e4[i]);
+            int4 q4[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) q4[c] = 4 * c < deg ? __ldg(row + c) : make_int4(-1, -1, -1, -1);
+            int w = lpos;
+            if (loads == 0) smm[w] = 0;  // a unit without loads keeps one slot
+            if (hasg) smm[w++] = (uint16_t)g;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int32_t hv[4] = {q4[c].x, q4[c].y, q4[c].z, q4[c].w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (4 * c + t < deg && hv[t] != f) smm[w++] = (uint16_t)hv[t];
+            }
+            sunit[pos] = make_uint2((uint32_t)f | ((uint32_t)hasg << 16) | ((uint32_t)kUnitWhole << 17),
+                                      (uint32_t)lpos | ((uint32_t)(deg - 1) << 20));
+        }
+    }
+    // ... chain links from the back, one thread a link
+    for (int j = tid; j < NS; j += T) {
+        const int h = segh[j];
+        const int2 x = hx[h];
+        int e, r;
+        if (!plan_link(segk, x, j, &e, &r)) continue;
+        const int4 hr = hrec[h];
+        const int32_t f = hr.x, g = hr.y;
+        const int hasg = g < a.n ? 1 : 0, loads = hasg + hr.w - 1;
+        const int S = plan_seg(loads);
+        const int s = j - x.x, key = (int)segk[j];
+        const int s0 = s * S, s1 = min(loads, (e + 1) * S);
+        const int hg = s == 0 ? hasg : 0, cnt = s1 - s0 - hg, last = e == x.y - 1 ? 1 : 0;
+        const int old = atomicAdd(cu + key, 0x10000);
+        const int pos = bu[key] + hu[key] - 1 - (old >> 16);
+        const int lpos = bl[key] + atomicAdd(cl + key, hg + (r > 0 ? 1 : 0) + cnt);
+        const uint16_t *ml = a.list + hr.z;
+        int w = lpos;
+        if (hg) smm[w++] = (uint16_t)g;
+        if (r > 0) smm[w++] = (uint16_t)f;
+        for (int qq = s0 + hg; qq < s1; qq += 8) {
+            uint16_t v[8];  // members loaded together
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = qq + t < s1 ? ml[qq + t - hasg] : 0;
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                if (qq + t < s1) smm[w + t] = v[t];
+            w += min(8, s1 - qq);
+        }
+        sunit[pos] = make_uint2((uint32_t)f | ((uint32_t)hg << 16) | ((uint32_t)kUnitChain << 17) |
+                                      ((uint32_t)r << 19) | ((uint32_t)last << 27),
+                                  (uint32_t)lpos | ((uint32_t)cnt << 20));
+    }
+    __syncthreads();
+    // E: units and loads out in 16-byte pieces (both arrays have room past
+    // the last piece)
+    {
+        const int4 *su = reinterpret_cast<const int4 *>(sunit);
+        int4 *du = reinterpret_cast<int4 *>(a.units);
+        for (int i = tid; i < (s_u + 1) / 2; i += T) du[i] = su[i];
+        const int4 *sm = reinterpret_cast<const int4 *>(smm);
+        int4 *dm = reinterpret_cast<int4 *>(a.mem);
+        for (int i = tid; i < (s_m + 7) / 8; i += T) dm[i] = sm[i];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        a.fhdr[kFhKeyFit] = 1;
+        __threadfence();
+        a.fhdr[kFhOk] = 1;
+    }
+}
+
 // Writes x_f of a finished check from its accumulator and marks it final
 // (the whole warp; every segment fenced before counting).
 __device__ __forceinline__ void flow_finish_slot(const PeelArgs &a, uint2 r, uint4 *accs, uint8_t *ready,
@@ -1824,6 +2169,167 @@ __device__ bool flow_body(const PeelArgs &a, int64_t slice) {
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// key walk
+//
+// The units of the dataflow plan (with every heavy pair chained: no check
+// slots) walked with one block barrier per key instead of ready flags. Key
+// k's units read only blocks that units of smaller keys finished (see the
+// plan above), so after the barrier that ends key k - 1 every unit of key k
+// may run at once, one item per (unit, word) as in the level walk: its loads
+// (c_g, the chain's partial sum, its members) all in flight, then one store.
+// The heavy gathers run while their members are fresh in L2, without the
+// flags, their polls or the batch masks. Stages: key k's units and loads are
+// bulk-copied into slot k % 3 two keys ahead (one mbarrier phase each), and
+// key k + 1's coded rows are prefetched into L2 while key k runs.
+
+constexpr int kKeyRound = 9;  // loads in flight per item (a chain link: its partial sum and 8 members)
+
+size_t keys_smem_bytes() {
+    return (size_t)kKeyMax * 32 + (size_t)3 * (kKeyUnits * 8 + kKeyMem * 2);
+}
+
+// One thread: bulk copies of key k's units and loads into slot k % 3.
+__device__ __forceinline__ void issue_key(const PeelArgs &a, const int4 *kt, int k, uint2 *sun,
+                                          uint16_t *smm, uint64_t *bar) {
+    const int4 t0 = kt[2 * k], t1 = kt[2 * k + 1];
+    const int sl = k % 3;
+    const uint32_t ub = (uint32_t)t0.w * 8, mb = (uint32_t)t1.y * 2;
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(bar, ub + mb);
+    if (ub) bulk_g2s(sun + sl * kKeyUnits, a.funits + t0.z, ub, bar);
+    if (mb) bulk_g2s(smm + sl * kKeyMem, a.fmem + t1.x, mb, bar);
+}
+
+// Returns false (the same answer in every thread, before anything is written
+// to global memory) when the path has no key-walk plan; the caller then walks
+// level by level.
+__device__ bool keys_body(const PeelArgs &a, int64_t slice) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mb_keys[3];
+    __shared__ int s_ok[2];  // by key parity: thread 0 writes the next while others read this one
+    const int32_t *fh = a.fhdr;
+    if (fh[kFhOk] != 1 || fh[kFhKeyFit] != 1) return false;
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int L = a.L;
+    const int64_t w0 = slice * L;
+    const int lanes = (int)min((int64_t)L, a.tw - w0);
+    const int nk = a.hdr[WS_N_LEVELS] + 1;
+    int4 *kt = reinterpret_cast<int4 *>(smem);                        // [2 kKeyMax]
+    uint2 *sun = reinterpret_cast<uint2 *>(kt + 2 * kKeyMax);          // [3][kKeyUnits]
+    uint16_t *smm = reinterpret_cast<uint16_t *>(sun + 3 * kKeyUnits);  // [3][kKeyMem]
+    for (int i = tid; i < 2 * nk; i += T) kt[i] = a.fktab[i];
+    if (tid == 0) {
+        for (int k = 0; k < 3; ++k) mbar_init(&mb_keys[k]);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_ok[0] = s_ok[1] = 1;
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < 2 && k < nk; ++k) issue_key(a, kt, k, sun, smm, &mb_keys[k]);
+    const int lines = (lanes * 16 + 127) >> 7;
+    // every thread keeps one word kk and takes units srow, srow + nrows, ...
+    // of each key, counted from the highest thread (as in the level walk)
+    const int rt0 = T - 1 - tid;
+    const int kk = rt0 % lanes, srow = rt0 / lanes, nrows = T / lanes;
+    bool ok = true;
+    for (int k = 0; k < nk; ++k) {
+        const int ps = k % 3;
+        if (tid == 0) {
+            // key k's stages are in; so are key k + 1's, whose coded rows are
+            // prefetched below
+            const uint32_t ph0 = (uint32_t)((k / 3) & 1), ph1 = (uint32_t)(((k + 1) / 3) & 1);
+            const bool in0 = mbar_wait(&mb_keys[ps], ph0);
+            const bool in1 = in0 && (k + 1 >= nk || mbar_wait(&mb_keys[(k + 1) % 3], ph1));
+            s_ok[k & 1] = in1 ? 1 : 0;
+            if (!in1) {
+                // give up, but first wait longer (8 bounds) for the copies
+                // not yet seen to land (keys k and k + 1; k + 2's is not
+                // issued yet)
+                if (!in0) mbar_wait(&mb_keys[ps], ph0, 8);
+                if (k + 1 < nk) mbar_wait(&mb_keys[(k + 1) % 3], ph1, 8);
+            }
+        }
+        __syncthreads();  // key k - 1 is written; key k's stages are in
+        if (!s_ok[k & 1]) {
+            ok = false;
+            break;
+        }
+        if (tid == 0 && k + 2 < nk) issue_key(a, kt, k + 2, sun, smm, &mb_keys[(k + 2) % 3]);
+        if (k + 1 < nk) {
+            // L2 prefetch of the coded rows key k + 1 reads (low threads; the
+            // items below start from the high ones)
+            const int q = (k + 1) % 3;
+            const int4 n0 = kt[2 * (k + 1)], n1 = kt[2 * (k + 1) + 1];
+            const uint2 *un = sun + q * kKeyUnits + (n0.x - n0.z);
+            for (int i = tid; i < n0.y * lines; i += T) {
+                const int j = i / lines, ln = i - j * lines;
+                const uint2 r = un[j];
+                if ((r.x >> 16) & 1u) {
+                    const int32_t g = smm[q * kKeyMem + (int)(r.y & kMoffMask) - n1.x];
+                    const char *p = reinterpret_cast<const char *>(a.coded + (int64_t)g * a.tw + w0) + 128 * ln;
+                    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+                }
+            }
+        }
+        const int4 t0 = kt[2 * k], t1 = kt[2 * k + 1];
+        const uint2 *ut = sun + ps * kKeyUnits + (t0.x - t0.z);
+        const uint16_t *mt = smm + ps * kKeyMem;
+        const uint64_t pol_last = l2_policy_last(), pol_first = l2_policy_first();
+        for (int j = (srow < nrows ? srow : t0.y); j < t0.y; j += nrows) {
+            const int64_t w = w0 + kk;
+            const uint2 r = ut[j];
+            // loads: c_g (hasg), the chain's partial sum (a link after the
+            // first), the members; none for a check without members (x_f = 0)
+            const int hasg = (int)((r.x >> 16) & 1u);
+            const int part = (((r.x >> 17) & 3u) == kUnitChain && ((r.x >> 19) & 0xffu) > 0) ? 1 : 0;
+            const int nl = hasg + part + (int)(r.y >> 20);
+            const int mo = (int)(r.y & kMoffMask) - t1.x;  // its first load in the stage
+            uint4 x[kKeyRound];  // the round's loads, all in flight at once
+#pragma unroll
+            for (int i = 0; i < kKeyRound; ++i) {
+                x[i] = make_uint4(0, 0, 0, 0);
+                if (i < nl) {
+                    const int32_t h = mt[mo + i];
+                    if (i == 0 && hasg) {
+                        const uint4 *src = a.coded + (int64_t)h * a.tw + w;
+                        x[i] = a.hints ? ld_nc_hint(src, pol_first) : src[0];
+                    } else {
+                        const uint4 *src = block_ptr(a, h) + w;
+                        x[i] = a.hints ? ld_hint(src, pol_last) : src[0];
+                    }
+                }
+            }
+            uint4 acc = x[0];
+#pragma unroll
+            for (int i = 1; i < kKeyRound; ++i) xor4(acc, x[i]);
+            // a link of more loads (equal keys merged): further rounds of 8
+            for (int j0 = kKeyRound; j0 < nl; j0 += 8) {
+                uint4 y[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    y[i] = make_uint4(0, 0, 0, 0);
+                    if (j0 + i < nl) y[i] = block_ptr(a, mt[mo + j0 + i])[w];
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) xor4(acc, y[i]);
+            }
+            uint4 *dst = block_ptr(a, (int32_t)(r.x & 0xffffu)) + w;
+            if (a.hints) st_hint(dst, acc, pol_last);
+            else dst[0] = acc;
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && !ok) atomicExch(a.status, FS_ERR_TIMEOUT);
+    // unrecovered data blocks read as zero
+    const int32_t nu = a.hdr[WS_N_UNREC_DATA];
+    for (int32_t it = tid; it < nu * lanes; it += T) {
+        const int32_t q = it / lanes, lane2 = it - q * lanes;
+        a.data[(int64_t)a.unrec_list[q] * a.tw + w0 + lane2] = make_uint4(0, 0, 0, 0);
+    }
+    return true;
+}
+
 // The level walk alone; k_peel_flow is the dataflow walk (its own kernel, so
 // its registers do not weigh on the level walk), which falls back to the
 // level walk when the path has no plan.
@@ -1831,6 +2337,12 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) { peel_bod
 
 __global__ void __launch_bounds__(kPeelThreads, 1) k_peel_flow(PeelArgs a) {
     if (flow_body(a, blockIdx.x)) return;
+    peel_body(a, blockIdx.x);
+}
+
+// the key walk, likewise falling back to the level walk
+__global__ void __launch_bounds__(kPeelThreads, 1) k_peel_keys(PeelArgs a) {
+    if (keys_body(a, blockIdx.x)) return;
     peel_body(a, blockIdx.x);
 }
 
@@ -1888,6 +2400,9 @@ DpgArgs dpg_args(const fs_code *c, const uint8_t *erased, uint8_t *ws, uint8_t *
     a.flow_hdr = reinterpret_cast<int32_t *>(ws + L.flow_hdr);
     a.flow_lvl = reinterpret_cast<uint16_t *>(ws + L.flow_lvl);
     a.flow_hist = reinterpret_cast<int32_t *>(ws + L.flow_hist);
+    const bool keys = c->peel_flow == 2 && !(c->peel_columns && col_fits(c)) && flow_applies(c);
+    a.flow_list = keys ? reinterpret_cast<uint16_t *>(ws + L.flow_list) : nullptr;
+    a.flow_pinfo = keys ? reinterpret_cast<uint32_t *>(ws + L.flow_pinfo) : nullptr;
     return a;
 }
 
@@ -1975,17 +2490,19 @@ PeelArgs peel_args(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_
     a.fbatch = reinterpret_cast<const uint4 *>(ws + L.flow_batch);
     a.fmem = reinterpret_cast<const uint16_t *>(ws + L.flow_mem);
     a.fslot = reinterpret_cast<const int32_t *>(ws + L.flow_slot);
+    a.fktab = reinterpret_cast<const int4 *>(ws + L.flow_ktab);
     return a;
 }
 
 }  // namespace
 
-// The dataflow walk applies to one 1024-thread CTA per SM, 16-bit block ids
+// The dataflow walks apply to one 1024-thread CTA per SM, 16-bit block ids
 // and levels, rows of at most kFlowMaxDeg and padded graphs whose offsets fit
-// 20 bits.
+// 20 bits (and the key walk to a device with room for its stages and its plan).
 bool flow_applies(const fs_code *c) {
     return c->peel_flow && c->peel_ctas == 1 && c->k_int <= 65535 && c->n_con <= 65535 &&
-           c->max_con_deg <= kFlowMaxDeg && c->e_con4 < (int64_t)kMoffMask;
+           c->max_con_deg <= kFlowMaxDeg && c->e_con4 < (int64_t)kMoffMask &&
+           (c->peel_flow != 2 || (keys_smem_bytes() <= c->smem_optin && key_plan_smem() <= c->smem_optin));
 }
 
 namespace {
@@ -1999,6 +2516,26 @@ size_t flow_smem(const fs_code *c) { return c->smem_optin & ~(size_t)15; }
 cudaError_t launch_flow_plan(const fs_code *c, uint8_t *ws, cudaStream_t s) {
     const DecodeLayout L = decode_layout(c);
     const int64_t Lw = peel_slice_words(c);
+    if (c->peel_flow == 2) {
+        // the key walk's plan: one CTA
+        KeyPlanArgs k;
+        k.hdr = reinterpret_cast<const int32_t *>(ws);
+        k.pair_rec = reinterpret_cast<const int4 *>(ws + L.pair_rec);
+        k.con_idx4 = c->con_idx4;
+        k.lvl = reinterpret_cast<const uint16_t *>(ws + L.flow_lvl);
+        k.list = reinterpret_cast<const uint16_t *>(ws + L.flow_list);
+        k.pinfo = reinterpret_cast<const uint32_t *>(ws + L.flow_pinfo);
+        k.n = c->n;
+        k.fhdr = reinterpret_cast<int32_t *>(ws + L.flow_hdr);
+        k.ktab = reinterpret_cast<int4 *>(ws + L.flow_ktab);
+        k.units = reinterpret_cast<uint2 *>(ws + L.flow_units);
+        k.mem = reinterpret_cast<uint16_t *>(ws + L.flow_mem);
+        const size_t ksm = key_plan_smem();
+        cudaError_t e = cudaFuncSetAttribute(k_key_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksm);
+        if (e != cudaSuccess) return e;
+        k_key_plan<<<1, kPlanThreads, ksm, s>>>(k);
+        return cudaGetLastError();
+    }
     const int slots = flow_slot_cap(Lw);
     const size_t smem = flow_smem(c);
     FlowUnitArgs u;
@@ -2054,12 +2591,13 @@ cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, u
     const int64_t Lw = a.L;
     size_t smem = peel_smem_bytes(Lw);
     if (flow_applies(c)) {
-        // all the shared memory the CTA may have: the plan's size depends on
-        // the path, which only the device knows (k_flow_plan checks it)
-        a.flow = 1;
-        smem = std::max(smem, flow_smem(c));
+        // the dataflow walk: all the shared memory the CTA may have (the
+        // plan's size depends on the path, which only the device knows;
+        // k_flow_place checks it); the key walk: its stages
+        a.flow = c->peel_flow;
+        smem = std::max(smem, a.flow == 2 ? keys_smem_bytes() : flow_smem(c));
     }
-    const auto kern = a.flow ? k_peel_flow : k_peel;
+    const auto kern = a.flow == 2 ? k_peel_keys : (a.flow ? k_peel_flow : k_peel);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // one CTA per SM: 1024 threads; several: the SM's threads split between them
@@ -2111,7 +2649,9 @@ cudaError_t decode_batch_plan(const fs_code *const *codes, const void *const *co
     for (int32_t i = 0; i < n; ++i) {
         const fs_code *c = codes[i];
         uint8_t *w = static_cast<uint8_t *>(ws[i]);
-        const DpgArgs a = dpg_args(c, erased[i], w, unrecovered[i], n_unrecovered[i]);
+        DpgArgs a = dpg_args(c, erased[i], w, unrecovered[i], n_unrecovered[i]);
+        a.flow_list = nullptr;  // the batch's payload walks level by level: no member order
+        a.flow_pinfo = nullptr;
         const DpgCompactPlace cp = plan_dpg_compact(c);
         if (c->dpg_compact && cp.bytes >= 0) {
             dc.push_back(a);

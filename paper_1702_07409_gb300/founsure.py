@@ -61,7 +61,8 @@ class _Csr(ctypes.Structure):
 class _PathView(ctypes.Structure):
     _fields_ = [("n_levels", ctypes.c_void_p), ("n_pairs", ctypes.c_void_p),
                 ("level_off", ctypes.c_void_p), ("pair_f", ctypes.c_void_p),
-                ("pair_g", ctypes.c_void_p), ("parity", ctypes.c_void_p)]
+                ("pair_g", ctypes.c_void_p), ("parity", ctypes.c_void_p),
+                ("plan", ctypes.c_void_p)]
 
 
 _lib = None
@@ -300,7 +301,8 @@ class Code:
 
     def decode_path(self, ws):
         """Views into a decode workspace after fs_decode (synchronises):
-        returns dict(n_levels, n_pairs, level_off, pair_f, pair_g, parity)."""
+        returns dict(n_levels, n_pairs, level_off, pair_f, pair_g, parity,
+        plan: the payload plan's 8-word header)."""
         import torch
         v = _PathView()
         _check(lib().fs_decode_path(self._h, _addr(ws), ctypes.byref(v)), "fs_decode_path")
@@ -318,7 +320,8 @@ class Code:
                     level_off=at(v.level_off, nl + 1, torch.int32),
                     pair_f=at(v.pair_f, npairs, torch.int32),
                     pair_g=at(v.pair_g, npairs, torch.int32),
-                    parity=at(v.parity, self.m * self.t, torch.uint8))
+                    parity=at(v.parity, self.m * self.t, torch.uint8),
+                    plan=at(v.plan, 8, torch.int32))
 
     def update(self, idx, n_idx: int, new, data, parity, coded, ws, stream=None) -> None:
         self._need(idx, 4 * n_idx, "idx")

@@ -82,6 +82,7 @@ def _check_decode(case, coded_np, coded_dev, erased):
         got = _host(view["parity"]).reshape(case.m, case.t)
         ok = path.unrecovered[case.b:] == 0
         assert np.array_equal(got[ok], par[ok])
+    path.plan = _host(view["plan"])
     return path
 
 
@@ -318,6 +319,7 @@ def _check_plain(g, t, erased, tuning=None):
         ok = path.unrecovered[g.b:] == 0
         assert np.array_equal(got[ok], par[ok])
     assert fs.Code.ws_status(ws) == fs.FS_OK
+    path.plan = _host(view["plan"])
     return path
 
 
@@ -366,11 +368,12 @@ def test_wide_check_level_splits_into_steps(cols, t):
 
 
 @pytest.mark.parametrize("knob,value", [(1, 2), (1, 4), (2, 1), (3, 0), (4, 1), (5, 0), (5, 2),
-                                        (5, 3), (7, 1), (8, 1)])
+                                        (5, 3), (7, 1), (8, 0), (8, 1)])
 def test_tuning_knobs_leave_results_unchanged(knob, value):
     """Payload CTAs per SM, one gather CTA per SM, general (not compact)
     decoding schedule, L2 eviction hints, row-gather encode, 16- and 32-byte
-    slice encode, column payload, the barrier-free (dataflow) payload walk."""
+    slice encode, column payload, the level walk and the barrier-free
+    (dataflow) walk instead of the default key walk."""
     import torch
     fs = _fs()
     case = Case(1500, 60, 2000, 4096 + 32, gen.DIST_FINITE40)
@@ -596,47 +599,63 @@ def test_chained_precode_validation():
         fs.Code(graph([[0, 1], [2, 3], [1, 2]]), 16)  # level 1 before level 0
 
 
+@pytest.mark.parametrize("walk", [0, 1, 2])
 @pytest.mark.parametrize("case", ["precoded_joint", "precoded_two_pass", "long_chain", "wide_checks",
                                   "rsd_plain", "array_precode", "config2"])
-def test_flow_payload_matches_oracle(case):
-    """The barrier-free payload walk (FS_TUNE_PEEL_FLOW = 1), byte for byte
-    against the oracle: precode checks summed in shared-memory slots and
-    heavy rows chained through their output block (precoded, both decoding
-    modes, several erasure rates), one symbol per level, checks of 32
-    members in one level, long RSD rows (units of more than one round of
-    loads), a chained (array) precode whose checks read parities, and the
-    full-size precoded stripe."""
+def test_flow_payload_matches_oracle(case, walk):
+    """The payload walks, byte for byte against the oracle: walk 0 (level
+    by level), walk 1 (FS_TUNE_PEEL_FLOW = 1, no level barriers; precode
+    checks summed in shared-memory slots) and walk 2 (the default key walk:
+    one barrier per level, every heavy pair chained through its output
+    block, its pieces in the member order the schedule recorded). Cases:
+    precoded, both decoding modes, several erasure rates; one symbol per
+    level (1100 keys: more than the key walk's table, so walk 2 falls back to
+    the level walk); checks of 32 members in one level; long RSD rows (units
+    of more than one round of loads); a chained (array) precode whose checks
+    read parities; the full-size precoded stripe. Walk 2 must have run on its
+    plan wherever it fits, and walk 0 made none (the plan header says so)."""
     fs = _fs()
-    flow = {fs.TUNE_PEEL_FLOW: 1}
+    flow = {fs.TUNE_PEEL_FLOW: walk}
+    paths = []
     if case.startswith("precoded"):
         c = Case(700, 40, 950, 272, gen.DIST_FINITE40, mode=1 if case.endswith("two_pass") else 0)
-        c.code.set_tuning(fs.TUNE_PEEL_FLOW, 1)
+        c.code.set_tuning(fs.TUNE_PEEL_FLOW, walk)
         _, p, cd = c.encode_gpu()
         _, cod = oracle.encode(c.g, c.data, c.t)
         for s, frac in enumerate((0.1, 0.2, 0.3)):
-            _check_decode(c, cod, cd, _erased(c.n, frac, gen.SEED_ERASE + (s << 20)))
+            paths.append(_check_decode(c, cod, cd, _erased(c.n, frac, gen.SEED_ERASE + (s << 20))))
     elif case == "long_chain":
         b = 1100
         g = _graph_from_rows(b, [[0]] + [[j - 1, j] for j in range(1, b)])
-        assert _check_plain(g, 32, np.zeros(b, np.uint8), flow).n_levels == b
+        path = _check_plain(g, 32, np.zeros(b, np.uint8), flow)
+        assert path.n_levels == b
+        if walk == 2:
+            assert path.plan[7] == 0  # no key walk: the level walk ran
     elif case == "wide_checks":
         b, m = 2048, 64
         g = _graph_from_rows(b, [[v] for v in range(b + m)],
                              [[j + 64 * i for i in range(32)] for j in range(m)])
         erased = np.zeros(b + m, np.uint8)
         erased[:64] = 1
-        assert not _check_plain(g, 4096 + 48, erased, flow).unrecovered.any()
+        path = _check_plain(g, 4096 + 48, erased, flow)
+        assert not path.unrecovered.any()
+        paths.append(path)
     elif case == "rsd_plain":
         g = gen.make_graph(2000, 0, 2600, gen.DIST_RSD, 0.05, 0.01)
         for s in range(2):
-            _check_plain(g, 1024 + 16, _erased(2600, 0.1, gen.SEED_ERASE + (s << 20)), flow)
+            paths.append(_check_plain(g, 1024 + 16, _erased(2600, 0.1, gen.SEED_ERASE + (s << 20)), flow))
     elif case == "array_precode":
         # p = 67, two levels of 67 checks (the second reads parities of the first)
         g = gen.make_graph_array(1005, 1139, 1481, gen.DIST_FINITE40)
-        _check_plain(g, 512, _erased(g.n, 0.15, gen.SEED_ERASE), flow)
+        paths.append(_check_plain(g, 512, _erased(g.n, 0.15, gen.SEED_ERASE), flow))
     else:
         c = Case(4096, 128, 5400, 65536, gen.DIST_FINITE40)
-        c.code.set_tuning(fs.TUNE_PEEL_FLOW, 1)
+        c.code.set_tuning(fs.TUNE_PEEL_FLOW, walk)
         _, p, cd = c.encode_gpu()
         _, cod = oracle.encode(c.g, c.data, c.t)
-        _check_decode(c, cod, cd, _erased(c.n, 0.2, gen.SEED_ERASE))
+        paths.append(_check_decode(c, cod, cd, _erased(c.n, 0.2, gen.SEED_ERASE)))
+    for path in paths:
+        if walk == 2 and path.n_pairs:
+            assert path.plan[2] == 1 and path.plan[7] == 1, path.plan
+        if walk == 0:
+            assert not path.plan.any(), path.plan  # no plan
