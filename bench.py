@@ -52,8 +52,8 @@ PEEL_TRAFFIC_BYTES = 645942272 + 311390720
 SLICES_TRAFFIC_BYTES = 273567232 + 310150912
 # the payload's walk (FS_TUNE_PEEL_FLOW; the library's default is 2): its
 # kernel, and the plan kernels the decoding schedule adds for it
-PEEL_KERNEL = {0: "k_peel", 1: "k_peel_flow", 2: "k_peel_keys"}
-PLAN_KERNELS = {0: [], 1: ["k_flow_units", "k_flow_place"], 2: ["k_key_plan"]}
+PEEL_KERNEL = {0: "k_peel", 1: "k_peel_flow", 2: "k_peel_keys", 3: "k_peel_keys"}
+PLAN_KERNELS = {0: [], 1: ["k_flow_units", "k_flow_place"], 2: ["k_key_plan"], 3: ["k_key_plan"]}
 DEFAULT_WALK = 2
 
 
@@ -1308,9 +1308,10 @@ def main():
                     help="requests of the serving object in the default line")
     ap.add_argument("--l2-hints", action="store_true",
                     help="tuning knob: L2 evict-last / evict-first hints")
-    ap.add_argument("--peel-flow", type=int, choices=[0, 1, 2], default=None,
+    ap.add_argument("--peel-flow", type=int, choices=[0, 1, 2, 3], default=None,
                     help="tuning knob FS_TUNE_PEEL_FLOW: 0 the level walk, 1 the dataflow walk "
-                         "without level barriers, 2 the key walk (default: the library's)")
+                         "without level barriers, 2 the key walk from 64 MiB of intermediates, "
+                         "3 the key walk at any size (default: the library's, 2)")
     ap.add_argument("--two-pass", action="store_true",
                     help="decode in the paper's two passes (LT code, then the precode) "
                          "instead of jointly")

@@ -146,11 +146,11 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
  *                        fs_decode / fs_decode_schedule (a payload without
  *                        the plan reports FS_ERR_INVALID in the workspace)
  *   FS_TUNE_PEEL_FLOW    how the slice payload walks the decoding path.
- *                        2 (default), the key walk: a heavy decoder (more
- *                        than 8 loads: precode checks, high-degree rows) is
- *                        gathered in pieces of 8 of its members, in the
- *                        order the schedule recovered them; each piece runs
- *                        right after the level that produced its last member
+ *                        The key walk: a heavy decoder (more than 8 loads:
+ *                        precode checks, high-degree rows) is gathered in
+ *                        pieces of 8 of its members, in the order the
+ *                        schedule recovered them; each piece runs right
+ *                        after the level that produced its last member
  *                        (while L2 still holds its members) and adds to a
  *                        partial sum kept in the output block; every other
  *                        pair is one gather at its own level; one barrier
@@ -159,18 +159,25 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
  *                        (about 25 us at 4096 x 64 KiB, n = 5400, 20%
  *                        erased, where the payload reads 0.65 GB from HBM
  *                        against 1.04 GB level by level and runs 12%
- *                        faster). 1: the same pieces without level
- *                        barriers, each gather waiting only for the blocks it
- *                        reads (fewer HBM bytes still, more instructions:
- *                        slower). 0: level by level, every pair whole.
- *                        Walks 1 and 2 apply to codes of at most 65535
+ *                        faster).
+ *                        2 (default): the key walk for codes whose
+ *                        intermediates reach 64 MiB (k_int x t), the level
+ *                        walk below that, where the recovered blocks stay in
+ *                        L2 anyway and the plan's fixed cost (about 10-40
+ *                        us) would not pay; 3: the key walk at any size;
+ *                        1: the same pieces without level barriers, each
+ *                        gather waiting only for the blocks it reads (fewer
+ *                        HBM bytes still, more instructions: slower);
+ *                        0: level by level, every pair whole.
+ *                        Walks 1 to 3 apply to codes of at most 65535
  *                        intermediates and constraints, rows of at most
- *                        4000 entries, FS_TUNE_PEEL_CTAS = 1 and the compact
- *                        schedule (walk 2), and to paths whose plan fits
- *                        the plan kernel's tables and the payload's stages
- *                        (at most 1024 levels); elsewhere the payload walks
- *                        level by level. Set it before fs_decode /
- *                        fs_decode_schedule (the schedule makes the plan)
+ *                        4000 entries and FS_TUNE_PEEL_CTAS = 1 (walks 2 and
+ *                        3 also to the compact schedule), and to paths whose
+ *                        plan fits the plan kernel's tables and the
+ *                        payload's stages (at most 1024 levels); elsewhere
+ *                        the payload walks level by level. Set it before
+ *                        fs_decode / fs_decode_schedule (the schedule makes
+ *                        the plan)
  * Returns FS_ERR_INVALID for an unknown knob or an out-of-range value. Not
  * thread-safe against concurrent hot calls on the same code. */
 #define FS_TUNE_PEEL_CTAS   1

@@ -271,7 +271,7 @@ FS_API fs_status fs_code_set_tuning(fs_code *c, int knob, int value) {
             c->peel_columns = value;
             return FS_OK;
         case FS_TUNE_PEEL_FLOW:
-            if (value < 0 || value > 2) return FS_ERR_INVALID;
+            if (value < 0 || value > 3) return FS_ERR_INVALID;
             c->peel_flow = value;
             return FS_OK;
     }

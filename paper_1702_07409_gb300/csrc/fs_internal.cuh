@@ -68,8 +68,9 @@ struct fs_code {
     int rows_per_ticket;  // coded rows per work ticket of the row-gather encode (1..16)
     int peel_columns;     // 1: column payload (every intermediate of a byte column in
                           // shared memory) when the code fits it; 0 (default): slice payload
-    int peel_flow;        // 2 (default): the key walk; 1: the dataflow walk without
-                          // level barriers; 0: the level walk
+    int peel_flow;        // 2 (default): the key walk for stripes of >= 64 MiB of
+                          // intermediates; 3: the key walk at any size; 1: the
+                          // dataflow walk without level barriers; 0: the level walk
                           // where its plan fits; 0 (default): level by level
     // slice encode tables (present when sl_slots > 0): every input block has
     // a 16-byte shared-memory slot per byte slice; data block v is slot v,

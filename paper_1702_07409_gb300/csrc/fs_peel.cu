@@ -2400,7 +2400,7 @@ DpgArgs dpg_args(const fs_code *c, const uint8_t *erased, uint8_t *ws, uint8_t *
     a.flow_hdr = reinterpret_cast<int32_t *>(ws + L.flow_hdr);
     a.flow_lvl = reinterpret_cast<uint16_t *>(ws + L.flow_lvl);
     a.flow_hist = reinterpret_cast<int32_t *>(ws + L.flow_hist);
-    const bool keys = c->peel_flow == 2 && !(c->peel_columns && col_fits(c)) && flow_applies(c);
+    const bool keys = c->peel_flow >= 2 && !(c->peel_columns && col_fits(c)) && flow_applies(c);
     a.flow_list = keys ? reinterpret_cast<uint16_t *>(ws + L.flow_list) : nullptr;
     a.flow_pinfo = keys ? reinterpret_cast<uint32_t *>(ws + L.flow_pinfo) : nullptr;
     return a;
@@ -2496,13 +2496,21 @@ PeelArgs peel_args(const fs_code *c, const uint4 *coded, uint4 *data_out, uint8_
 
 }  // namespace
 
+// The key walk by default (FS_TUNE_PEEL_FLOW = 2) only where the
+// intermediates reach 64 MiB: below that the recovered blocks stay in L2 for
+// the level walk too, and the schedule's member order and the plan kernel
+// (~10-40 us) would not pay; 3 takes it at any size.
+constexpr int64_t kKeyWalkMinBytes = (int64_t)64 << 20;
+
 // The dataflow walks apply to one 1024-thread CTA per SM, 16-bit block ids
 // and levels, rows of at most kFlowMaxDeg and padded graphs whose offsets fit
 // 20 bits (and the key walk to a device with room for its stages and its plan).
 bool flow_applies(const fs_code *c) {
+    const bool keys = c->peel_flow >= 2;
     return c->peel_flow && c->peel_ctas == 1 && c->k_int <= 65535 && c->n_con <= 65535 &&
            c->max_con_deg <= kFlowMaxDeg && c->e_con4 < (int64_t)kMoffMask &&
-           (c->peel_flow != 2 || (keys_smem_bytes() <= c->smem_optin && key_plan_smem() <= c->smem_optin));
+           (!keys || (keys_smem_bytes() <= c->smem_optin && key_plan_smem() <= c->smem_optin)) &&
+           (c->peel_flow != 2 || (int64_t)c->k_int * c->t >= kKeyWalkMinBytes);
 }
 
 namespace {
@@ -2516,7 +2524,7 @@ size_t flow_smem(const fs_code *c) { return c->smem_optin & ~(size_t)15; }
 cudaError_t launch_flow_plan(const fs_code *c, uint8_t *ws, cudaStream_t s) {
     const DecodeLayout L = decode_layout(c);
     const int64_t Lw = peel_slice_words(c);
-    if (c->peel_flow == 2) {
+    if (c->peel_flow >= 2) {
         // the key walk's plan: one CTA
         KeyPlanArgs k;
         k.hdr = reinterpret_cast<const int32_t *>(ws);
@@ -2594,7 +2602,7 @@ cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, u
         // the dataflow walk: all the shared memory the CTA may have (the
         // plan's size depends on the path, which only the device knows;
         // k_flow_place checks it); the key walk: its stages
-        a.flow = c->peel_flow;
+        a.flow = std::min(c->peel_flow, 2);  // 3: the key walk at any size
         smem = std::max(smem, a.flow == 2 ? keys_smem_bytes() : flow_smem(c));
     }
     const auto kern = a.flow == 2 ? k_peel_keys : (a.flow ? k_peel_flow : k_peel);

@@ -83,6 +83,7 @@ def _check_decode(case, coded_np, coded_dev, erased):
         ok = path.unrecovered[case.b:] == 0
         assert np.array_equal(got[ok], par[ok])
     path.plan = _host(view["plan"])
+    path.big = (case.b + case.m) * case.t >= 64 << 20  # the default key walk's size
     return path
 
 
@@ -320,6 +321,7 @@ def _check_plain(g, t, erased, tuning=None):
         assert np.array_equal(got[ok], par[ok])
     assert fs.Code.ws_status(ws) == fs.FS_OK
     path.plan = _host(view["plan"])
+    path.big = (g.b + g.m) * t >= 64 << 20  # the default key walk's size
     return path
 
 
@@ -368,12 +370,13 @@ def test_wide_check_level_splits_into_steps(cols, t):
 
 
 @pytest.mark.parametrize("knob,value", [(1, 2), (1, 4), (2, 1), (3, 0), (4, 1), (5, 0), (5, 2),
-                                        (5, 3), (7, 1), (8, 0), (8, 1)])
+                                        (5, 3), (7, 1), (8, 0), (8, 1), (8, 3)])
 def test_tuning_knobs_leave_results_unchanged(knob, value):
     """Payload CTAs per SM, one gather CTA per SM, general (not compact)
     decoding schedule, L2 eviction hints, row-gather encode, 16- and 32-byte
-    slice encode, column payload, the level walk and the barrier-free
-    (dataflow) walk instead of the default key walk."""
+    slice encode, column payload, the level walk, the barrier-free
+    (dataflow) walk and the key walk at this size (the default keeps it for
+    larger stripes)."""
     import torch
     fs = _fs()
     case = Case(1500, 60, 2000, 4096 + 32, gen.DIST_FINITE40)
@@ -599,21 +602,24 @@ def test_chained_precode_validation():
         fs.Code(graph([[0, 1], [2, 3], [1, 2]]), 16)  # level 1 before level 0
 
 
-@pytest.mark.parametrize("walk", [0, 1, 2])
+@pytest.mark.parametrize("walk", [0, 1, 2, 3])
 @pytest.mark.parametrize("case", ["precoded_joint", "precoded_two_pass", "long_chain", "wide_checks",
                                   "rsd_plain", "array_precode", "config2"])
 def test_flow_payload_matches_oracle(case, walk):
     """The payload walks, byte for byte against the oracle: walk 0 (level
     by level), walk 1 (FS_TUNE_PEEL_FLOW = 1, no level barriers; precode
-    checks summed in shared-memory slots) and walk 2 (the default key walk:
-    one barrier per level, every heavy pair chained through its output
-    block, its pieces in the member order the schedule recorded). Cases:
+    checks summed in shared-memory slots), walk 3 (the key walk: one barrier
+    per level, every heavy pair chained through its output block, its pieces
+    in the member order the schedule recorded) and walk 2 (the default: the
+    key walk from 64 MiB of intermediates, here only the full-size stripe,
+    the level walk below). Cases:
     precoded, both decoding modes, several erasure rates; one symbol per
-    level (1100 keys: more than the key walk's table, so walk 2 falls back to
+    level (1100 keys: more than the key walk's table, so walk 3 falls back to
     the level walk); checks of 32 members in one level; long RSD rows (units
     of more than one round of loads); a chained (array) precode whose checks
     read parities; the full-size precoded stripe. Walk 2 must have run on its
-    plan wherever it fits, and walk 0 made none (the plan header says so)."""
+    plan wherever it fits, and walks 0 (and 2 below its size) made none (the
+    plan header says so)."""
     fs = _fs()
     flow = {fs.TUNE_PEEL_FLOW: walk}
     paths = []
@@ -629,7 +635,7 @@ def test_flow_payload_matches_oracle(case, walk):
         g = _graph_from_rows(b, [[0]] + [[j - 1, j] for j in range(1, b)])
         path = _check_plain(g, 32, np.zeros(b, np.uint8), flow)
         assert path.n_levels == b
-        if walk == 2:
+        if walk >= 2:
             assert path.plan[7] == 0  # no key walk: the level walk ran
     elif case == "wide_checks":
         b, m = 2048, 64
@@ -655,7 +661,8 @@ def test_flow_payload_matches_oracle(case, walk):
         _, cod = oracle.encode(c.g, c.data, c.t)
         paths.append(_check_decode(c, cod, cd, _erased(c.n, 0.2, gen.SEED_ERASE)))
     for path in paths:
-        if walk == 2 and path.n_pairs:
+        keys = walk == 3 or (walk == 2 and path.big)
+        if keys and path.n_pairs:
             assert path.plan[2] == 1 and path.plan[7] == 1, path.plan
-        if walk == 0:
+        if walk == 0 or (walk == 2 and not path.big):
             assert not path.plan.any(), path.plan  # no plan
