@@ -48,8 +48,8 @@ METRIC = "encode & BP-decode source GB/s"
 #       --clock-control none -k regex:"k_peel|k_slices|k_key_plan" -s 9 -c 3
 #       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-extras
 # on one GB300. Valid only while those two kernels are unchanged.
-PEEL_TRAFFIC_BYTES = 645942272 + 311390720
-SLICES_TRAFFIC_BYTES = 273567232 + 310150912
+PEEL_TRAFFIC_BYTES = 644593152 + 310951424
+SLICES_TRAFFIC_BYTES = 273551616 + 310546944
 # the payload's walk (FS_TUNE_PEEL_FLOW; the library's default is 2): its
 # kernel, and the plan kernels the decoding schedule adds for it
 PEEL_KERNEL = {0: "k_peel", 1: "k_peel_flow", 2: "k_peel_keys", 3: "k_peel_keys"}

@@ -105,6 +105,7 @@ __device__ __forceinline__ Ticket ticket_of(const RowArgs &a, int32_t t, int32_t
     return k;
 }
 
+template <bool kHints>
 __device__ __forceinline__ void store_row(const RowArgs &a, int32_t row, int64_t w0, int64_t w1,
                                           const uint4 *acc, uint64_t pol_out) {
     uint4 *out = a.out + (int64_t)row * a.tw;
@@ -112,7 +113,7 @@ __device__ __forceinline__ void store_row(const RowArgs &a, int32_t row, int64_t
     for (int v = 0; v < kEncV; ++v) {
         const int64_t w = w0 + threadIdx.x + (int64_t)v * kEncThreads;
         if (w >= w1) continue;
-        if (a.hints) st_hint(out + w, acc[v], pol_out);
+        if (kHints) st_hint(out + w, acc[v], pol_out);
         else if (a.stream_out) __stcs(out + w, acc[v]);
         else __stcg(out + w, acc[v]);
     }
@@ -130,7 +131,10 @@ __device__ __forceinline__ int find_job(const RowArgs *jobs, int n_jobs, int32_t
 }
 
 // Tickets run job by job (a stripe's chunks one after the other), so the
-// resident CTAs work on one stripe's byte range at a time.
+// resident CTAs work on one stripe's byte range at a time. kHints: L2
+// eviction hints (FS_TUNE_L2_HINTS), a template parameter so the default
+// path carries no per-load branch or policy registers for them.
+template <bool kHints>
 __device__ __forceinline__ void rows_body(const RowArgs *jobs, int n_jobs, int32_t n_tickets,
                                           int32_t *ticket_ctr) {
     // ring of 3 pointer stages (two tickets ahead), 2 neighbour stages, 4 tickets
@@ -205,8 +209,8 @@ __device__ __forceinline__ void rows_body(const RowArgs *jobs, int n_jobs, int32
             ok[v] = w[v] < w1;
             acc[v] = make_uint4(0, 0, 0, 0);
         }
-        const uint64_t pol_in = l2_policy_last();
-        const uint64_t pol_out = a.stream_out ? l2_policy_first() : l2_policy_last();
+        const uint64_t pol_in = kHints ? l2_policy_last() : 0;
+        const uint64_t pol_out = kHints ? (a.stream_out ? l2_policy_first() : l2_policy_last()) : 0;
         int r = 0;  // row being accumulated; entries [rp[r], rp[r + 1])
         for (int32_t e = e_base; e < e_end; e += 8) {
             uint4 x[8][kEncV];
@@ -218,15 +222,15 @@ __device__ __forceinline__ void rows_body(const RowArgs *jobs, int n_jobs, int32
                                                : a.inB + (int64_t)(v - a.split) * a.tw;
 #pragma unroll
                 for (int q = 0; q < kEncV; ++q)
-                    x[j][q] = (on && ok[q]) ? (a.hints ? ld_nc_hint(src + w[q], pol_in)
-                                                       : __ldg(src + w[q]))
+                    x[j][q] = (on && ok[q]) ? (kHints ? ld_nc_hint(src + w[q], pol_in)
+                                                      : __ldg(src + w[q]))
                                             : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 if (e + j >= e_end) break;
                 while (e + j >= rp[r + 1]) {  // row r is complete (rows may be empty)
-                    store_row(a, k.r0 + r, w0, w1, acc, pol_out);
+                    store_row<kHints>(a, k.r0 + r, w0, w1, acc, pol_out);
 #pragma unroll
                     for (int v = 0; v < kEncV; ++v) acc[v] = make_uint4(0, 0, 0, 0);
                     ++r;
@@ -236,7 +240,7 @@ __device__ __forceinline__ void rows_body(const RowArgs *jobs, int n_jobs, int32
             }
         }
         for (; r < k.nr; ++r) {  // the last row with entries, then empty rows
-            store_row(a, k.r0 + r, w0, w1, acc, pol_out);
+            store_row<kHints>(a, k.r0 + r, w0, w1, acc, pol_out);
 #pragma unroll
             for (int v = 0; v < kEncV; ++v) acc[v] = make_uint4(0, 0, 0, 0);
         }
@@ -245,15 +249,16 @@ __device__ __forceinline__ void rows_body(const RowArgs *jobs, int n_jobs, int32
 }
 
 // one job, passed by value
+template <bool kHints>
 __global__ void __launch_bounds__(kEncThreads, kCtasPerSm)
     k_rows(const __grid_constant__ RowArgs a, int32_t n_tickets, int32_t *ticket_ctr) {
-    rows_body(&a, 1, n_tickets, ticket_ctr);
+    rows_body<kHints>(&a, 1, n_tickets, ticket_ctr);
 }
 
-// a batch of jobs (stripes) in device memory
+// a batch of jobs (stripes) in device memory (batches take no L2 hints)
 __global__ void __launch_bounds__(kEncThreads, kCtasPerSm)
     k_rows_batch(const RowArgs *jobs, int n_jobs, int32_t n_tickets, int32_t *ticket_ctr) {
-    rows_body(jobs, n_jobs, n_tickets, ticket_ctr);
+    rows_body<false>(jobs, n_jobs, n_tickets, ticket_ctr);
 }
 
 // ---- shared-memory slice encode --------------------------------------------
@@ -1084,8 +1089,8 @@ cudaError_t launch_encode(const fs_code *c, const void *data, void *parity, void
             if (l > 0) e = cudaMemsetAsync(hdr + WS_COUNT_A, 0, sizeof(int32_t), s);
             if (e != cudaSuccess) return e;
             const int64_t tickets = (int64_t)n_chunks * a.n_rows;
-            k_rows<<<grid_for(tickets, c->num_sms, ctas), kEncThreads, 0, s>>>(a, (int32_t)tickets,
-                                                                              hdr + WS_COUNT_A);
+            (c->l2_hints ? k_rows<true> : k_rows<false>)<<<grid_for(tickets, c->num_sms, ctas), kEncThreads,
+                                                             0, s>>>(a, (int32_t)tickets, hdr + WS_COUNT_A);
             e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
@@ -1102,8 +1107,8 @@ cudaError_t launch_encode(const fs_code *c, const void *data, void *parity, void
         a.rows = c->rows_per_ticket;
         a.t0 = 0;
         const int64_t tickets = (int64_t)n_chunks * ((c->n + a.rows - 1) / a.rows);
-        k_rows<<<grid_for(tickets, c->num_sms, ctas), kEncThreads, 0, s>>>(a, (int32_t)tickets,
-                                                                          hdr + WS_COUNT_B);
+        (c->l2_hints ? k_rows<true> : k_rows<false>)<<<grid_for(tickets, c->num_sms, ctas), kEncThreads, 0,
+                                                         s>>>(a, (int32_t)tickets, hdr + WS_COUNT_B);
         e = cudaGetLastError();
     }
     return e;
