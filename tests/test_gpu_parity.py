@@ -604,7 +604,8 @@ def test_chained_precode_validation():
 
 @pytest.mark.parametrize("walk", [0, 1, 2, 3])
 @pytest.mark.parametrize("case", ["precoded_joint", "precoded_two_pass", "long_chain", "wide_checks",
-                                  "rsd_plain", "array_precode", "config2"])
+                                  "rsd_plain", "array_precode", "config2", "plan_overflow",
+                                  "general_schedule"])
 def test_flow_payload_matches_oracle(case, walk):
     """The payload walks, byte for byte against the oracle: walk 0 (level
     by level), walk 1 (FS_TUNE_PEEL_FLOW = 1, no level barriers; precode
@@ -617,9 +618,12 @@ def test_flow_payload_matches_oracle(case, walk):
     level (1100 keys: more than the key walk's table, so walk 3 falls back to
     the level walk); checks of 32 members in one level; long RSD rows (units
     of more than one round of loads); a chained (array) precode whose checks
-    read parities; the full-size precoded stripe. Walk 2 must have run on its
-    plan wherever it fits, and walks 0 (and 2 below its size) made none (the
-    plan header says so)."""
+    read parities; the full-size precoded stripe; a path whose key plan
+    exceeds the plan kernel's tables (8000 pairs, 47 K loads) and the general
+    (not compact) schedule, which records no member order: walks 2 and 3 fall
+    back to the level walk there. Walk 3 must have run on its plan wherever it
+    fits, and walks 0 (and 2 below its size) made none (the plan header says
+    so)."""
     fs = _fs()
     flow = {fs.TUNE_PEEL_FLOW: walk}
     paths = []
@@ -650,6 +654,21 @@ def test_flow_payload_matches_oracle(case, walk):
         g = gen.make_graph(2000, 0, 2600, gen.DIST_RSD, 0.05, 0.01)
         for s in range(2):
             paths.append(_check_plain(g, 1024 + 16, _erased(2600, 0.1, gen.SEED_ERASE + (s << 20)), flow))
+    elif case == "plan_overflow":
+        g = gen.make_graph(8000, 0, 10400, gen.DIST_RSD, 0.05, 0.01)
+        path = _check_plain(g, 64, _erased(10400, 0.1, gen.SEED_ERASE), flow)
+        assert path.n_pairs == 8000
+        if walk >= 2:
+            assert path.plan[7] == 0  # no key walk: the level walk ran
+    elif case == "general_schedule":
+        c = Case(700, 40, 950, 272, gen.DIST_FINITE40)
+        c.code.set_tuning(fs.TUNE_PEEL_FLOW, walk)
+        c.code.set_tuning(fs.TUNE_DPG_COMPACT, 0)
+        _, p, cd = c.encode_gpu()
+        _, cod = oracle.encode(c.g, c.data, c.t)
+        path = _check_decode(c, cod, cd, _erased(c.n, 0.2, gen.SEED_ERASE))
+        if walk >= 2:
+            assert path.plan[7] == 0  # no member order: the level walk ran
     elif case == "array_precode":
         # p = 67, two levels of 67 checks (the second reads parities of the first)
         g = gen.make_graph_array(1005, 1139, 1481, gen.DIST_FINITE40)
