@@ -54,6 +54,9 @@ SLICES_TRAFFIC_BYTES = 273551616 + 310546944
 # kernel, and the plan kernels the decoding schedule adds for it
 PEEL_KERNEL = {0: "k_peel", 1: "k_peel_flow", 2: "k_peel_keys", 3: "k_peel_keys"}
 PLAN_KERNELS = {0: [], 1: ["k_flow_units", "k_flow_place"], 2: ["k_key_plan"], 3: ["k_key_plan"]}
+# the key walk's payload is followed by a level-walk launch that returns at
+# once where the key walk had its plan
+FALLBACK_KERNELS = {0: [], 1: [], 2: ["k_peel"], 3: ["k_peel"]}
 DEFAULT_WALK = 2
 
 
@@ -424,7 +427,8 @@ def run_gpu(args):
                 "copies": "uploads and read-backs on two copy streams, overlapping the "
                           "neighbouring steps' kernels (two input sets)",
                 "readback_verified": e2e_ok},
-        "gpu_launches": (Stripe.LAUNCHES_PER_STEP + len(PLAN_KERNELS[walk_of(args)])) * K,
+        "gpu_launches": (Stripe.LAUNCHES_PER_STEP + len(PLAN_KERNELS[walk_of(args)]) +
+                         len(FALLBACK_KERNELS[walk_of(args)])) * K,
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                    "reasons": clocks["reasons"]},
     }

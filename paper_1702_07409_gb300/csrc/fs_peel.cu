@@ -1247,9 +1247,10 @@ enum { kFhUnits = 0, kFhLoads = 1, kFhOk = 2, kFhSlots = 3, kFhBatches = 4, kFhS
        kFhOverflow = 6, kFhKeyFit = 7 };
 // the key walk's shared-memory stages (one key each): units (from an even
 // index) and loads (from a multiple of 8), and the key table
-constexpr int kKeyUnits = 4096;
-constexpr int kKeyMem = 8192;
-constexpr int kKeyMax = 1024;  // 176 KiB of stages in all
+constexpr int kKeyUnits = 1024;
+constexpr int kKeyMem = 4096;
+constexpr int kKeyMax = 1024;  // 80 KiB of stages in all: the rest of the SM's
+                               // shared memory serves as L1 for the gathers
 
 // Loads of a unit: c_g, the chain's partial sum, its members; a unit with
 // none (a check of no members decoding its parity: the zero block) keeps one
@@ -2338,8 +2339,13 @@ __device__ bool keys_body(const PeelArgs &a, int64_t slice) {
 // The level walk alone; k_peel_flow is the dataflow walk (its own kernel, so
 // its registers do not weigh on the level walk), which falls back to the
 // level walk when the path has no plan.
+// The level walk; after k_peel_keys (a.flow == 2) it runs only where the key
+// walk had no plan (the same answer in every thread).
 template <bool kHints>
-__global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) { peel_body<kHints>(a, blockIdx.x); }
+__global__ void __launch_bounds__(kPeelThreads, 1) k_peel(PeelArgs a) {
+    if (a.flow == 2 && a.fhdr[kFhOk] == 1 && a.fhdr[kFhKeyFit] == 1) return;
+    peel_body<kHints>(a, blockIdx.x);
+}
 
 template <bool kHints>
 __global__ void __launch_bounds__(kPeelThreads, 1) k_peel_flow(PeelArgs a) {
@@ -2347,11 +2353,12 @@ __global__ void __launch_bounds__(kPeelThreads, 1) k_peel_flow(PeelArgs a) {
     peel_body<kHints>(a, blockIdx.x);
 }
 
-// the key walk, likewise falling back to the level walk
+// the key walk; where its plan is missing it does nothing, and k_peel,
+// launched right after it, walks level by level (the level walk's stages
+// would make this launch's shared memory, and so take L1 from the gathers)
 template <bool kHints>
 __global__ void __launch_bounds__(kPeelThreads, 1) k_peel_keys(PeelArgs a) {
-    if (keys_body<kHints>(a, blockIdx.x)) return;
-    peel_body<kHints>(a, blockIdx.x);
+    keys_body<kHints>(a, blockIdx.x);
 }
 
 // one CTA per (stripe, slice) item of a batch
@@ -2610,20 +2617,30 @@ cudaError_t launch_peel(const fs_code *c, const uint4 *coded, uint4 *data_out, u
     if (flow_applies(c)) {
         // the dataflow walk: all the shared memory the CTA may have (the
         // plan's size depends on the path, which only the device knows;
-        // k_flow_place checks it); the key walk: its stages
+        // k_flow_place checks it)
         a.flow = std::min(c->peel_flow, 2);  // 3: the key walk at any size
-        smem = std::max(smem, a.flow == 2 ? keys_smem_bytes() : flow_smem(c));
+        if (a.flow == 1) smem = std::max(smem, flow_smem(c));
     }
     const bool h = a.hints != 0;
-    const auto kern = a.flow == 2   ? (h ? k_peel_keys<true> : k_peel_keys<false>)
-                      : a.flow == 1 ? (h ? k_peel_flow<true> : k_peel_flow<false>)
-                                    : (h ? k_peel<true> : k_peel<false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     // one CTA per SM: 1024 threads; several: the SM's threads split between them
     const int threads =
         c->peel_ctas >= 4 ? kPeelThreads / 4 : (c->peel_ctas >= 2 ? kPeelThreads / 2 : kPeelThreads);
     const int64_t n_slices = (c->tw + Lw - 1) / Lw;
+    cudaError_t e;
+    if (a.flow == 2) {
+        // the key walk on its own stages, then the level walk where it had
+        // no plan (an empty launch where it had one)
+        const auto kk = h ? k_peel_keys<true> : k_peel_keys<false>;
+        const size_t ks = keys_smem_bytes();
+        e = cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks);
+        if (e != cudaSuccess) return e;
+        kk<<<(unsigned)n_slices, threads, ks, s>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const auto kern = a.flow == 1 ? (h ? k_peel_flow<true> : k_peel_flow<false>) : (h ? k_peel<true> : k_peel<false>);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     kern<<<(unsigned)n_slices, threads, smem, s>>>(a);
     return cudaGetLastError();
 }

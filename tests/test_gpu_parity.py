@@ -616,7 +616,8 @@ def test_flow_payload_matches_oracle(case, walk):
     the level walk below). Cases:
     precoded, both decoding modes, several erasure rates; one symbol per
     level (1100 keys: more than the key walk's table, so walk 3 falls back to
-    the level walk); checks of 32 members in one level; long RSD rows (units
+    the level walk); checks of 32 members in one level (after a level of 2112
+    pairs, more than the key walk's stage: walk 3 falls back); long RSD rows (units
     of more than one round of loads); a chained (array) precode whose checks
     read parities; the full-size precoded stripe; a path whose key plan
     exceeds the plan kernel's tables (8000 pairs, 47 K loads) and the general
@@ -649,7 +650,12 @@ def test_flow_payload_matches_oracle(case, walk):
         erased[:64] = 1
         path = _check_plain(g, 4096 + 48, erased, flow)
         assert not path.unrecovered.any()
-        paths.append(path)
+        if walk >= 2:
+            # level 0 holds 2112 whole pairs, more than the key walk's stage
+            # of 1024 units: the level walk ran
+            assert path.plan[7] == 0
+        else:
+            paths.append(path)
     elif case == "rsd_plain":
         g = gen.make_graph(2000, 0, 2600, gen.DIST_RSD, 0.05, 0.01)
         for s in range(2):
