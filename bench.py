@@ -45,11 +45,11 @@ METRIC = "encode & BP-decode source GB/s"
 # the payload (k_peel_keys, the default key walk) and of the slice encode
 # (k_slices) at this workload, taken with
 #   ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum
-#       --clock-control none -k regex:"k_peel|k_slices|k_key_plan" -s 9 -c 3
+#       --clock-control none -k regex:"k_peel|k_slices|k_key_plan" -s 12 -c 4
 #       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-extras
 # on one GB300. Valid only while those two kernels are unchanged.
-PEEL_TRAFFIC_BYTES = 644593152 + 310951424
-SLICES_TRAFFIC_BYTES = 273551616 + 310546944
+PEEL_TRAFFIC_BYTES = 649066240 + 310867200
+SLICES_TRAFFIC_BYTES = 273362176 + 310039040
 # the payload's walk (FS_TUNE_PEEL_FLOW; the library's default is 2): its
 # kernel, and the plan kernels the decoding schedule adds for it
 PEEL_KERNEL = {0: "k_peel", 1: "k_peel_flow", 2: "k_peel_keys", 3: "k_peel_keys"}
