@@ -889,8 +889,8 @@ struct PeelArgs {
     int32_t L;  // words of every block per CTA
     int32_t hints;  // 1: gathered / recovered blocks evict-last, coded payloads evict-first
     int32_t *status;
-    // dataflow walk (flow_body) when 1, key walk (keys_body) when 2, on the
-    // plan of k_flow_units / k_flow_place
+    // dataflow walk (flow_body, on the plan of k_flow_units / k_flow_place)
+    // when 1, key walk (keys_body, on the plan of k_key_plan) when 2
     int32_t flow;
     int32_t k_int;
     const int32_t *fhdr, *fslot;
@@ -2177,16 +2177,16 @@ __device__ bool flow_body(const PeelArgs &a, int64_t slice) {
 // ---------------------------------------------------------------------------
 // key walk
 //
-// The units of the dataflow plan (with every heavy pair chained: no check
-// slots) walked with one block barrier per key instead of ready flags. Key
-// k's units read only blocks that units of smaller keys finished (see the
-// plan above), so after the barrier that ends key k - 1 every unit of key k
-// may run at once, one item per (unit, word) as in the level walk: its loads
-// (c_g, the chain's partial sum, its members) all in flight, then one store.
-// The heavy gathers run while their members are fresh in L2, without the
-// flags, their polls or the batch masks. Stages: key k's units and loads are
-// bulk-copied into slot k % 3 two keys ahead (one mbarrier phase each), and
-// key k + 1's coded rows are prefetched into L2 while key k runs.
+// The units of the key walk's plan (k_key_plan below: every heavy pair
+// chained, units keyed like the dataflow plan's) walked with one block
+// barrier per key (= level). Key k's units read only blocks that units of
+// smaller keys finished, so after the barrier that ends key k - 1 every unit
+// of key k may run at once, one item per (unit, word) as in the level walk:
+// its loads (c_g, the chain's partial sum, its members) all in flight, then
+// one store. The heavy gathers run while their members are fresh in L2.
+// Stages: key k's units and loads are bulk-copied into slot k % 3 two keys
+// ahead (one mbarrier phase each), and key k + 1's coded rows are prefetched
+// into L2 while key k runs.
 
 constexpr int kKeyRound = 9;  // loads in flight per item (a chain link: its partial sum and 8 members)
 
@@ -2207,8 +2207,8 @@ __device__ __forceinline__ void issue_key(const PeelArgs &a, const int4 *kt, int
 }
 
 // Returns false (the same answer in every thread, before anything is written
-// to global memory) when the path has no key-walk plan; the caller then walks
-// level by level.
+// to global memory) when the path has no key-walk plan; the level walk then
+// runs in the launch that follows (k_peel).
 template <bool kHints>
 __device__ bool keys_body(const PeelArgs &a, int64_t slice) {
     extern __shared__ __align__(16) unsigned char smem[];
