@@ -127,6 +127,20 @@ def test_config2_full_size_encode_decode():
     _check_decode(case, cod, cd, _erased(case.n, 0.2, gen.SEED_ERASE + (2 << 20)))
 
 
+def test_config2_full_size_two_pass_key_walk():
+    """The full-size precoded stripe decoded in the paper's two passes (the
+    LT rows to their fixpoint, then the checks) by the default payload, the
+    key walk, whose plan must have been made (this draw leaves 87
+    intermediates that the joint decoder recovers); a second draw too."""
+    case = Case(4096, 128, 5400, 65536, gen.DIST_FINITE40, mode=1)
+    _, p, cd = case.encode_gpu()
+    _, cod = oracle.encode(case.g, case.data, case.t)
+    path = _check_decode(case, cod, cd, _erased(case.n, 0.2, gen.SEED_ERASE))
+    assert path.n_pairs > 4000
+    assert path.plan[2] == 1 and path.plan[7] == 1, path.plan
+    _check_decode(case, cod, cd, _erased(case.n, 0.2, gen.SEED_ERASE + (2 << 20)))
+
+
 def test_update_and_repair_rounds():
     """Config-4 shape at reduced t: rewrite 1% of data, then repair 5% of coded."""
     import torch
