@@ -127,9 +127,12 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
  *                        all rows of that slice from it, when the code fits
  *                        (about 7000 data blocks + parities): 32-byte
  *                        slices when two buffers of them fit in shared
- *                        memory, else 16-byte slices; 2: always 16-byte
- *                        slices; 3: always 32-byte slices (when they fit);
- *                        0: row-gather encode through L2
+ *                        memory, or when d_coded is 32-byte aligned, t is a
+ *                        multiple of 32 and the stripe has at least 8
+ *                        slices per SM (each coded row's piece then goes out
+ *                        as one 256-bit store), else 16-byte slices; 2:
+ *                        always 16-byte slices; 3: always 32-byte slices
+ *                        (when they fit); 0: row-gather encode through L2
  *   FS_TUNE_ROWS_PER_TICKET 1..16 (default 16): coded rows per work ticket of
  *                        the row-gather encode (single calls and batches);
  *                        fewer rows per ticket keep the tickets in flight on a
