@@ -48,8 +48,8 @@ METRIC = "encode & BP-decode source GB/s"
 #       --clock-control none -k regex:"k_peel|k_slices|k_key_plan" -s 12 -c 4
 #       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-extras
 # on one GB300. Valid only while those two kernels are unchanged.
-PEEL_TRAFFIC_BYTES = 649066240 + 310867200
-SLICES_TRAFFIC_BYTES = 273362176 + 310039040
+PEEL_TRAFFIC_BYTES = 649121024 + 310724096
+SLICES_TRAFFIC_BYTES = 268601600 + 313820160
 # the payload's walk (FS_TUNE_PEEL_FLOW; the library's default is 2): its
 # kernel, and the plan kernels the decoding schedule adds for it
 PEEL_KERNEL = {0: "k_peel", 1: "k_peel_flow", 2: "k_peel_keys", 3: "k_peel_keys"}
@@ -417,7 +417,7 @@ def run_gpu(args):
                      "unit": "GB/s", "frac": round(dec_gbs / peak, 4),
                      "traffic": PEEL_TRAFFIC_BYTES if T == 65536 and walk_of(args) == DEFAULT_WALK else None,
                      "algorithmic_bytes": dec_bytes},
-        "encode_roofline": {"bound": "hbm", "kernel": "k_slices (fs_encode)",
+        "encode_roofline": {"bound": "hbm", "kernel": "k_slices<2> (fs_encode)",
                             "achieved": round(enc_gbs, 1), "peak": peak, "unit": "GB/s",
                             "frac": round(enc_gbs / peak, 4),
                             "traffic": SLICES_TRAFFIC_BYTES if T == 65536 else None,
