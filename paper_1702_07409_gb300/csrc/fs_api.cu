@@ -48,6 +48,7 @@ void free_code(fs_code *c) {
     cudaFree(c->con_ptr);
     cudaFree(c->con_idx);
     cudaFree(c->con_xs);
+    cudaFree(c->con_sum);
     cudaFree(c->pre_ptr);
     cudaFree(c->pre_idx);
     cudaFree(c->var_ptr);
@@ -129,13 +130,19 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
         con_idx[o++] = b + j;  // larger than every member: rows stay ascending
         con_ptr[n + j + 1] = (int32_t)o;
     }
-    // per constraint: degree bound and the XOR of its variable indices (the
-    // symbolic peel keeps this XOR over the still-unknown variables, so a
-    // constraint with one unknown names it without a scan)
-    std::vector<int32_t> con_xs((size_t)n_con, 0);
+    // per constraint: degree bound, and the XOR and the sum of its variable
+    // indices (the symbolic peel keeps one of them over the still-unknown
+    // variables, so a constraint with one unknown names it without a scan;
+    // rows are strictly ascending, so no index is counted twice)
+    std::vector<int32_t> con_xs((size_t)n_con, 0), con_sum((size_t)n_con, 0);
     for (int32_t g = 0; g < n_con; ++g) {
         max_con_deg = std::max(max_con_deg, con_ptr[g + 1] - con_ptr[g]);
-        for (int32_t e = con_ptr[g]; e < con_ptr[g + 1]; ++e) con_xs[g] ^= con_idx[e];
+        uint32_t sum = 0;
+        for (int32_t e = con_ptr[g]; e < con_ptr[g + 1]; ++e) {
+            con_xs[g] ^= con_idx[e];
+            sum += (uint32_t)con_idx[e];
+        }
+        con_sum[g] = (int32_t)sum;
     }
     // transpose: constraints containing each intermediate, ascending
     std::vector<int32_t> var_ptr((size_t)k_int + 1, 0), var_idx((size_t)e_con);
@@ -208,6 +215,7 @@ FS_API fs_status fs_code_create(const fs_csr *precode, const fs_csr *lt, size_t 
     if (e == cudaSuccess) e = upload(&c->con_ptr, con_ptr);
     if (e == cudaSuccess) e = upload(&c->con_idx, con_idx);
     if (e == cudaSuccess) e = upload(&c->con_xs, con_xs);
+    if (e == cudaSuccess) e = upload(&c->con_sum, con_sum);
     if (e == cudaSuccess) e = upload(&c->pre_ptr, pre_ptr);
     if (e == cudaSuccess) e = upload(&c->pre_idx, pre_idx);
     if (e == cudaSuccess) e = upload(&c->var_ptr, var_ptr);

@@ -49,6 +49,7 @@ struct fs_code {
     int32_t *con_ptr;     // [n_con + 1]
     int32_t *con_idx;     // [e_con]
     int32_t *con_xs;      // [n_con] XOR of the variable indices of each constraint
+    int32_t *con_sum;     // [n_con] sum of the variable indices of each constraint (mod 2^32)
     int32_t *con_ptr4;    // [n_con + 1] row starts of con_idx4 (multiples of 4)
     int32_t *con_idx4;    // rows of the joint graph padded to 16 bytes with -1
     int64_t e_con4;       // entries of con_idx4

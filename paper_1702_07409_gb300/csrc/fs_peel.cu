@@ -18,15 +18,19 @@
 //   level uses only symbols decoded in earlier levels (Section 3.1, first
 //   rule). Appends to the shared lists are warp-aggregated.
 //   k_dpg_compact (graphs with at most 65536 intermediates and constraints)
-//   keeps every per-level access in shared memory: 16-bit indices, res and
-//   xs packed in one word (claim bit | res << 16 | xs: a decrement touches
-//   only the res field, the XOR only the low half), 32-bit keys and a shared
-//   copy of the transposed graph. Its step C runs one thread per adjacency
-//   slot in two passes: fire-and-forget shared reductions, then plain loads
-//   find the constraints left with one unknown; each claims itself once (a
-//   claim bit) and at once bids for the next level, so step A of a level is
-//   done by the previous level's step C. k_dpg is the general form, with its
-//   state spilled to the workspace when needed.
+//   keeps every per-level access in shared memory: 16-bit indices, 32-bit
+//   keys, a shared copy of the transposed graph, and per constraint one word
+//   (sum << 16 | res) where sum is the SUM of the unknown indices mod 2^16
+//   instead of their XOR: decoding member f subtracts (f << 16) + 1 in one
+//   atomic (res >= 1 before it, so the low field never borrows into sum), and
+//   the value it returns is the constraint's state just before that update.
+//   The one update that takes res from 2 to 1 therefore knows the last
+//   unknown (sum - f, indices below 2^16) and bids for it at once, unless
+//   that unknown is decoded in the same level (then res reaches 0 in this
+//   step C too). Step C is one pass, one thread per adjacency slot, and step
+//   A of a level is done by the previous level's step C: two block barriers
+//   per level. k_dpg is the general form, with its state spilled to the
+//   workspace when needed.
 //
 // k_peel: the payload. Each CTA owns one slice of L 16-byte words of every
 //   block (about one CTA per SM, so every slice is in flight at once) and
@@ -138,10 +142,6 @@ __device__ __forceinline__ int find_slot(const int32_t *off, int n, int32_t x) {
     return lo;
 }
 
-__device__ __forceinline__ uint32_t smem_addr_u(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
 template <typename T>
 __device__ __forceinline__ T *place(unsigned char *smem, int32_t off, T *global) {
     return off >= 0 ? reinterpret_cast<T *>(smem + off) : global;
@@ -161,9 +161,12 @@ constexpr int kFlowHdrList = 8;
 // constraints whose members the compact schedule lists in recovery order:
 // those a pair of which can have more than 8 loads (kFlowSeg)
 constexpr int kListDeg = 9;
+// adjacency slots of one level that the compact schedule maps to their pair
+// without a search
+constexpr int kSlotCap = 4096;
 
 struct DpgArgs {
-    const int32_t *con_ptr, *con_ptr4, *con_xs, *var_ptr, *var_idx;
+    const int32_t *con_ptr, *con_ptr4, *con_xs, *con_sum, *var_ptr, *var_idx;
     const uint8_t *erased;
     int32_t b, n, k_int, n_con;
     int two_pass;
@@ -304,11 +307,13 @@ __device__ int warps_excl_scan1(int x, int *total, int (*s_warp)[32], int buf, i
 // level, 0} (format_path turns the stubs into the payload's records after
 // the walk), f's level for the dataflow plan, and the level-relative offset
 // of f's adjacency slots into lvl_v for step C (lvl_v[nt] = the level's
-// total, also in *s_tot: read it after the next block barrier). Called by
-// every thread; only the warps holding pairs scan.
+// total, also in *s_tot: read it after the next block barrier). Pair i also
+// writes i into slots[u] for each of its slots u below kSlotCap, so step C
+// finds a slot's pair without a search when the level's total fits. Called
+// by every thread; only the warps holding pairs scan.
 template <typename PairOf>
 __device__ void emit_pairs(const DpgArgs &a, LevelCursor &cur, int nt, PairOf pair_of, int32_t *lvl_v,
-                           int (*s_warp1)[32], int *s_tot) {
+                           uint16_t *slots, int (*s_warp1)[32], int *s_tot) {
     int len = 0;
     for (int base = 0; base < nt; base += blockDim.x) {
         const int nw = (min(nt - base, (int)blockDim.x) + 31) >> 5;  // warps holding pairs
@@ -328,7 +333,11 @@ __device__ void emit_pairs(const DpgArgs &a, LevelCursor &cur, int nt, PairOf pa
         }
         int total;
         const int off = warps_excl_scan1(vdeg, &total, s_warp1, buf, nw);
-        if (i < nt) lvl_v[i] = len + off;
+        if (i < nt) {
+            lvl_v[i] = len + off;
+            for (int u = len + off, u1 = min(len + off + vdeg, kSlotCap); u < u1; ++u)
+                slots[u] = (uint16_t)i;
+        }
         len += total;
     }
     if (threadIdx.x == 0) {  // warp 0 holds pairs whenever nt > 0
@@ -680,31 +689,20 @@ struct DpgCompactPlace {
         bytes;
 };
 
-constexpr int kSlotCap = 4096;        // adjacency slots of one level mapped without search
-constexpr uint32_t kClaim = 0x80000000u;  // pk bit: constraint already appended to a frontier
-
-__device__ __forceinline__ void red_xor_shared(uint32_t *p, uint32_t v) {
-    asm volatile("red.shared.xor.b32 [%0], %1;\n" ::"r"(smem_addr_u(p)), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ void red_add_shared(uint32_t *p, uint32_t v) {
-    asm volatile("red.shared.add.u32 [%0], %1;\n" ::"r"(smem_addr_u(p)), "r"(v) : "memory");
-}
-
 __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgCompactPlace &pl) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_warp1[2][32];
     __shared__ int2 s_w2[32];
     __shared__ int s_tot, s_max[4];
     // symbols of the next level, by level parity (a level reads one list
-    // while its step C2 fills the other)
+    // while its step C fills the other)
     __shared__ int s_nt[2], s_cnt, s_cnt_data;
     constexpr uint32_t kE = 0xffffffffu;
 
     const int tid = threadIdx.x, T = blockDim.x;
     const int32_t K = a.k_int, G = a.n_con;
     uint32_t *best = reinterpret_cast<uint32_t *>(smem + pl.best);
-    uint32_t *pk = reinterpret_cast<uint32_t *>(smem + pl.pk);  // claim | res << 16 | xs
+    uint32_t *pk = reinterpret_cast<uint32_t *>(smem + pl.pk);  // sum << 16 | res
     uint16_t *touched2 = reinterpret_cast<uint16_t *>(smem + pl.front);  // [2][K + 1]
     uint8_t *known = smem + pl.known;
     int32_t *cptr4 = reinterpret_cast<int32_t *>(smem + pl.cptr4);
@@ -715,12 +713,9 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
     int32_t *lvl_v = reinterpret_cast<int32_t *>(smem + pl.lvl_v);
     uint16_t *slots = reinterpret_cast<uint16_t *>(smem + pl.slots);  // [kSlotCap]
 
-    // A constraint c with one unknown left joins the bidding once: the
-    // thread that sets its claim bit bids key = (degree, c) for its unknown;
-    // the first bid for a symbol lists the symbol for the level.
-    auto claim_and_bid = [&](int32_t c, int list) {
-        if ((atomicOr(pk + c, kClaim) & kClaim) != 0) return;
-        const int32_t f = (int32_t)(pk[c] & 0xffffu);
+    // Constraint c, left with the one unknown f, bids key = (degree, c) for
+    // it; the first bid for f lists f for the level.
+    auto bid = [&](int32_t c, uint32_t f, int list) {
         const uint32_t key = ((uint32_t)deg[c] << 16) | (uint32_t)c;
         if (atomicMin(best + f, key) == kE)
             touched2[(size_t)list * (K + 1) + append_slot(&s_nt[list])] = (uint16_t)f;
@@ -738,14 +733,14 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
     for (int32_t g = tid; g < G; g += T) {
         const uint32_t d = (uint32_t)(__ldg(a.con_ptr + g + 1) - __ldg(a.con_ptr + g));
         deg[g] = (uint16_t)d;
-        pk[g] = (d << 16) | ((uint32_t)__ldg(a.con_xs + g) & 0xffffu);
+        pk[g] = ((uint32_t)__ldg(a.con_sum + g) << 16) | d;
         ok[g] = (g < a.n) ? (a.erased[g] == 0) : 1;
     }
     int stage = a.two_pass ? 0 : -1;
     if (tid == 0) s_nt[0] = s_nt[1] = 0;
     __syncthreads();
     for (int32_t g = tid; g < G; g += T)
-        if (usable(a, ok, g, stage) && (pk[g] >> 16) == 1) claim_and_bid(g, 0);
+        if (usable(a, ok, g, stage) && (pk[g] & 0xffffu) == 1) bid(g, pk[g] >> 16, 0);
     __syncthreads();
 
     LevelCursor cur;
@@ -756,15 +751,16 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
         if (nt == 0) {
             if (stage != 0) break;
             // two-pass: the coded rows reached their fixpoint; peel the checks
+            // (those left with one unknown during the first stage bid now)
             stage = 1;
             __syncthreads();  // every thread has read the empty count
             for (int32_t g = a.n + tid; g < G; g += T)
-                if (((pk[g] >> 16) & 0x7fffu) == 1) claim_and_bid(g, par);
+                if ((pk[g] & 0xffffu) == 1) bid(g, pk[g] >> 16, par);
             __syncthreads();
             continue;
         }
-        // B: pairs of the level (adjacency slots into lvl_v for step C); their
-        // records for the payload are formatted after the walk
+        // B: pairs of the level (adjacency slots into lvl_v and slots for
+        // step C); their records for the payload are formatted after the walk
         emit_pairs(
             a, cur, nt,
             [&](int i, int32_t *f, int32_t *g, int32_t *vdeg) {
@@ -772,7 +768,7 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
                 *g = (int32_t)(best[*f] & 0xffffu);
                 *vdeg = vptr[*f + 1] - vptr[*f];
             },
-            lvl_v, s_warp1, &s_tot);
+            lvl_v, slots, s_warp1, &s_tot);
         for (int i = tid; i < nt; i += T) {
             const int32_t f = touched[i];
             best[f] = kE;
@@ -780,48 +776,25 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
         }
         if (tid == 0) s_nt[par ^ 1] = 0;  // the list the next level's bids fill
         __syncthreads();
-        const int4 len = make_int4(0, 0, 0, s_tot);  // adjacency slots of the level
-        const bool mapped = len.w <= kSlotCap;  // uniform: slots of each pair listed
-        if (mapped) {
-            for (int i = tid; i < nt; i += T) {
-                const int32_t f = touched[i];
-                for (int32_t u = lvl_v[i], u1 = lvl_v[i] + vptr[f + 1] - vptr[f]; u < u1; ++u)
-                    slots[u] = (uint16_t)i;
-            }
-            __syncthreads();
-        }
-        // C1: one thread per adjacency slot: res -= 1 and xs ^= f on one
-        // constraint containing a newly decoded symbol, without waiting for
-        // a result; the slot's constraint is remembered for C2
-        for (int32_t u = tid; u < len.w; u += T) {
+        const int32_t len = s_tot;  // adjacency slots of the level
+        const bool mapped = len <= kSlotCap;  // uniform: every slot's pair in slots
+        // C (and step A of the next level): one thread per adjacency slot
+        // removes the newly decoded f from one constraint c containing it;
+        // the update that leaves c one unknown bids for it, unless that
+        // unknown is decoded in this level too
+        for (int32_t u = tid; u < len; u += T) {
             const int i = mapped ? (int)slots[u] : find_slot(lvl_v, nt, u);
             const int32_t f = touched[i];
             const int32_t c = vidx[vptr[f] + (u - lvl_v[i])];
-            red_xor_shared(pk + c, (uint32_t)f);
-            if (a.flow_list && deg[c] >= kListDeg) {
-                // f is the (deg - res)-th member of c to be recovered
-                const uint32_t old = atomicAdd(pk + c, 0xffff0000u);
-                a.flow_list[cptr4[c] + (int)deg[c] - (int)((old >> 16) & 0x7fffu)] = (uint16_t)f;
-            } else {
-                red_add_shared(pk + c, 0xffff0000u);  // -(1 << 16): decrement res
+            const uint32_t old = atomicAdd(pk + c, 0u - (((uint32_t)f << 16) + 1u));
+            const uint32_t res = old & 0xffffu;
+            // f is the (deg - res)-th member of c to be recovered
+            if (a.flow_list && deg[c] >= kListDeg)
+                a.flow_list[cptr4[c] + (int)deg[c] - (int)res] = (uint16_t)f;
+            if (res == 2) {
+                const uint32_t last = ((old >> 16) - (uint32_t)f) & 0xffffu;
+                if (!known[last] && usable(a, ok, c, stage)) bid(c, last, par ^ 1);
             }
-            if (mapped) slots[u] = (uint16_t)c;
-        }
-        __syncthreads();
-        // C2 (and step A of the next level): a touched constraint left with
-        // one unknown claims itself once and bids for that unknown
-        for (int32_t u = tid; u < len.w; u += T) {
-            int32_t c;
-            if (mapped) {
-                c = slots[u];
-            } else {
-                const int i = find_slot(lvl_v, nt, u);
-                const int32_t f = touched[i];
-                c = vidx[vptr[f] + (u - lvl_v[i])];
-            }
-            const uint32_t w = pk[c];
-            if ((w & kClaim) == 0 && (w >> 16) == 1 && usable(a, ok, c, stage))
-                claim_and_bid(c, par ^ 1);
         }
         __syncthreads();
         cur.np += nt;
@@ -850,8 +823,8 @@ DpgCompactPlace plan_dpg_compact(const fs_code *c) {
     DpgCompactPlace p;
     p.bytes = -1;
     const int64_t K = c->k_int, G = c->n_con;
-    // 16-bit indices; degrees below 2^15 (bit 31 of the packed word is the claim bit)
-    if (K > 65536 || G > 65536 || c->max_con_deg > 32767) return p;
+    // 16-bit indices; degrees below 2^16 (the res field of the packed word)
+    if (K > 65536 || G > 65536 || c->max_con_deg > 65535) return p;
     int64_t o = 0;
     auto take = [&](int64_t bytes) {
         const int64_t at = o;
@@ -1780,7 +1753,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_key_plan(KeyPlanArgs a) {
     }
     __syncthreads();
     if (s_bad) return;  // no plan (every thread)
-    const int NH = s_nh, NS = s_ns;
+    const int NS = s_ns;
 
     // B: segment keys, one thread a segment: the level of the segment's last
     // member (its highest: the members come by ascending level) + 1
@@ -2387,6 +2360,7 @@ DpgArgs dpg_args(const fs_code *c, const uint8_t *erased, uint8_t *ws, uint8_t *
     a.con_ptr = c->con_ptr;
     a.con_ptr4 = c->con_ptr4;
     a.con_xs = c->con_xs;
+    a.con_sum = c->con_sum;
     a.var_ptr = c->var_ptr;
     a.var_idx = c->var_idx;
     a.erased = erased;
