@@ -27,10 +27,12 @@
 //   The one update that takes res from 2 to 1 therefore knows the last
 //   unknown (sum - f, indices below 2^16) and bids for it at once, unless
 //   that unknown is decoded in the same level (then res reaches 0 in this
-//   step C too). Step C is one pass, one thread per adjacency slot, and step
-//   A of a level is done by the previous level's step C: two block barriers
-//   per level. k_dpg is the general form, with its state spilled to the
-//   workspace when needed.
+//   step C too). Step C is one pass with S threads per pair (S = 2^k <=
+//   T / pairs of the level), each taking every S-th constraint of its
+//   pair, so no scan places the level's adjacency slots; step A of a level
+//   is done by the previous level's step C: two block barriers per level.
+//   k_dpg is the general form, with its state spilled to the workspace when
+//   needed.
 //
 // k_peel: the payload. Each CTA owns one slice of L 16-byte words of every
 //   block (about one CTA per SM, so every slice is in flight at once) and
@@ -60,6 +62,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kDpgThreads = 1024;  // fills an SM's registers: no other kernel's CTA shares it
+static_assert((kDpgThreads & (kDpgThreads - 1)) == 0, "the compact schedule splits the CTA in powers of two");
 constexpr int kPeelThreads = 1024;  // 64 registers a thread: one item (segment, word) each
 constexpr int kPeelLmax = 64;       // largest slice (words) of one payload CTA
 constexpr int kStagePairs = 256;    // pairs of one level held in shared memory
@@ -131,17 +134,6 @@ __device__ int4 warps_excl_scan4(int4 x, int4 *total, int4 (*s_warp)[32], int bu
     return make_int4(b.x + v.x - x.x, b.y + v.y - x.y, b.z + v.z - x.z, b.w + v.w - x.w);
 }
 
-// Largest i in [0, n) with off[i] <= x, for ascending off[0] <= x.
-__device__ __forceinline__ int find_slot(const int32_t *off, int n, int32_t x) {
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= x) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
-
 template <typename T>
 __device__ __forceinline__ T *place(unsigned char *smem, int32_t off, T *global) {
     return off >= 0 ? reinterpret_cast<T *>(smem + off) : global;
@@ -161,9 +153,6 @@ constexpr int kFlowHdrList = 8;
 // constraints whose members the compact schedule lists in recovery order:
 // those a pair of which can have more than 8 loads (kFlowSeg)
 constexpr int kListDeg = 9;
-// adjacency slots of one level that the compact schedule maps to their pair
-// without a search
-constexpr int kSlotCap = 4096;
 
 struct DpgArgs {
     const int32_t *con_ptr, *con_ptr4, *con_xs, *con_sum, *var_ptr, *var_idx;
@@ -272,79 +261,6 @@ __device__ __forceinline__ void advance(LevelCursor &cur, int nt, const int4 &le
     cur.sb += (len.y + 3) & ~3;  // each level's segment list starts 16-byte aligned
     cur.cb += ((len.x >> 2) + 3) & ~3;  // ... and its chunk list
     ++cur.level;
-}
-
-// Exclusive prefix sum of one counter over the first nw warps of the block
-// (the warps holding items), like warps_excl_scan4; *total receives the sum.
-// Consecutive calls alternate buf.
-__device__ int warps_excl_scan1(int x, int *total, int (*s_warp)[32], int buf, int nw) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int v = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-    }
-    if (nw == 1) {
-        *total = __shfl_sync(0xffffffffu, v, 31);
-        return v - x;
-    }
-    if (lane == 31) s_warp[buf][wid] = v;
-    asm volatile("bar.sync 1, %0;\n" ::"r"(nw * 32) : "memory");
-    const int t = lane < nw ? s_warp[buf][lane] : 0;
-    int b = lane < wid ? t : 0, all = t;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        all += __shfl_xor_sync(0xffffffffu, all, o);
-    }
-    *total = all;
-    return b + v - x;
-}
-
-// Step B of a level in the compact form: only what the next levels need.
-// The level's pairs go out as pair_f / pair_g and a record stub {f, g,
-// level, 0} (format_path turns the stubs into the payload's records after
-// the walk), f's level for the dataflow plan, and the level-relative offset
-// of f's adjacency slots into lvl_v for step C (lvl_v[nt] = the level's
-// total, also in *s_tot: read it after the next block barrier). Pair i also
-// writes i into slots[u] for each of its slots u below kSlotCap, so step C
-// finds a slot's pair without a search when the level's total fits. Called
-// by every thread; only the warps holding pairs scan.
-template <typename PairOf>
-__device__ void emit_pairs(const DpgArgs &a, LevelCursor &cur, int nt, PairOf pair_of, int32_t *lvl_v,
-                           uint16_t *slots, int (*s_warp1)[32], int *s_tot) {
-    int len = 0;
-    for (int base = 0; base < nt; base += blockDim.x) {
-        const int nw = (min(nt - base, (int)blockDim.x) + 31) >> 5;  // warps holding pairs
-        const int buf = cur.scan_buf;
-        cur.scan_buf ^= 1;
-        if ((int)(threadIdx.x >> 5) >= nw) continue;
-        const int i = base + threadIdx.x;
-        int32_t vdeg = 0;
-        if (i < nt) {
-            int32_t f, g;
-            pair_of(i, &f, &g, &vdeg);
-            const int32_t p = cur.np + i;
-            a.pair_f[p] = f;
-            a.pair_g[p] = g;
-            a.pair_rec[2 * (size_t)p] = make_int4(f, g, cur.level, 0);
-            a.flow_lvl[f] = (uint16_t)cur.level;
-        }
-        int total;
-        const int off = warps_excl_scan1(vdeg, &total, s_warp1, buf, nw);
-        if (i < nt) {
-            lvl_v[i] = len + off;
-            for (int u = len + off, u1 = min(len + off + vdeg, kSlotCap); u < u1; ++u)
-                slots[u] = (uint16_t)i;
-        }
-        len += total;
-    }
-    if (threadIdx.x == 0) {  // warp 0 holds pairs whenever nt > 0
-        a.level_off[cur.level] = cur.np;
-        lvl_v[nt] = len;
-        *s_tot = len;
-    }
 }
 
 // Block-wide exclusive scan of two counters (x, y); *tot receives the sums.
@@ -685,15 +601,13 @@ DpgPlace plan_dpg(const fs_code *c) {
 }
 
 struct DpgCompactPlace {
-    int32_t best, pk, front, next, touched, known, cptr4, vptr, vidx, ok, lvl_v, deg, slots,
-        bytes;
+    int32_t best, pk, front, next, touched, known, cptr4, vptr, vidx, ok, deg, bytes;
 };
 
 __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgCompactPlace &pl) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_warp1[2][32];
     __shared__ int2 s_w2[32];
-    __shared__ int s_tot, s_max[4];
+    __shared__ int s_max[4];
     // symbols of the next level, by level parity (a level reads one list
     // while its step C fills the other)
     __shared__ int s_nt[2], s_cnt, s_cnt_data;
@@ -710,8 +624,6 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
     uint16_t *vidx = reinterpret_cast<uint16_t *>(smem + pl.vidx);
     uint16_t *deg = reinterpret_cast<uint16_t *>(smem + pl.deg);
     uint8_t *ok = smem + pl.ok;
-    int32_t *lvl_v = reinterpret_cast<int32_t *>(smem + pl.lvl_v);
-    uint16_t *slots = reinterpret_cast<uint16_t *>(smem + pl.slots);  // [kSlotCap]
 
     // Constraint c, left with the one unknown f, bids key = (degree, c) for
     // it; the first bid for f lists f for the level.
@@ -759,41 +671,58 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
             __syncthreads();
             continue;
         }
-        // B: pairs of the level (adjacency slots into lvl_v and slots for
-        // step C); their records for the payload are formatted after the walk
-        emit_pairs(
-            a, cur, nt,
-            [&](int i, int32_t *f, int32_t *g, int32_t *vdeg) {
-                *f = touched[i];
-                *g = (int32_t)(best[*f] & 0xffffu);
-                *vdeg = vptr[*f + 1] - vptr[*f];
-            },
-            lvl_v, slots, s_warp1, &s_tot);
+        // B: pairs of the level; their records for the payload are formatted
+        // after the walk (here only a stub {f, g, level, 0}), and f's level
+        // goes to the dataflow plan
         for (int i = tid; i < nt; i += T) {
             const int32_t f = touched[i];
+            const int32_t g = (int32_t)(best[f] & 0xffffu);
+            const int32_t p = cur.np + i;
+            a.pair_f[p] = f;
+            a.pair_g[p] = g;
+            a.pair_rec[2 * (size_t)p] = make_int4(f, g, cur.level, 0);
+            a.flow_lvl[f] = (uint16_t)cur.level;
             best[f] = kE;
             known[f] = 1;
         }
-        if (tid == 0) s_nt[par ^ 1] = 0;  // the list the next level's bids fill
+        if (tid == 0) {
+            a.level_off[cur.level] = cur.np;
+            s_nt[par ^ 1] = 0;  // the list the next level's bids fill
+        }
         __syncthreads();
-        const int32_t len = s_tot;  // adjacency slots of the level
-        const bool mapped = len <= kSlotCap;  // uniform: every slot's pair in slots
-        // C (and step A of the next level): one thread per adjacency slot
-        // removes the newly decoded f from one constraint c containing it;
-        // the update that leaves c one unknown bids for it, unless that
-        // unknown is decoded in this level too
-        for (int32_t u = tid; u < len; u += T) {
-            const int i = mapped ? (int)slots[u] : find_slot(lvl_v, nt, u);
-            const int32_t f = touched[i];
-            const int32_t c = vidx[vptr[f] + (u - lvl_v[i])];
-            const uint32_t old = atomicAdd(pk + c, 0u - (((uint32_t)f << 16) + 1u));
+        // C (and step A of the next level): S threads per pair, thread j of
+        // a pair takes its adjacency slots j, j + S, ... and removes f from
+        // each constraint c there; the update that leaves c one unknown bids
+        // for it, unless that unknown is decoded in this level too
+        auto update = [&](int32_t c, uint32_t f, uint32_t old) {
             const uint32_t res = old & 0xffffu;
             // f is the (deg - res)-th member of c to be recovered
             if (a.flow_list && deg[c] >= kListDeg)
                 a.flow_list[cptr4[c] + (int)deg[c] - (int)res] = (uint16_t)f;
             if (res == 2) {
-                const uint32_t last = ((old >> 16) - (uint32_t)f) & 0xffffu;
+                const uint32_t last = ((old >> 16) - f) & 0xffffu;
                 if (!known[last] && usable(a, ok, c, stage)) bid(c, last, par ^ 1);
+            }
+        };
+        // S = 2^k threads per pair, the largest with S * nt <= T (T is a
+        // power of two, so S divides T and the rounds of R = T / S pairs
+        // give every slot to exactly one thread); uniform, no division
+        const int k = max(0, (31 - __clz(T)) - (32 - __clz(nt - 1)));
+        const int S = 1 << k, R = T >> k;
+        for (int i = tid >> k; i < nt; i += R) {
+            const uint32_t f = touched[i];
+            const uint32_t dec = 0u - ((f << 16) + 1u);
+            const int32_t e1 = vptr[f + 1];
+            // two slots per round trip: both atomics in flight before either
+            // result is tested
+            for (int32_t e = vptr[f] + (tid & (S - 1)); e < e1; e += 2 * S) {
+                const int32_t c0 = vidx[e];
+                const bool two = e + S < e1;
+                const int32_t c1 = two ? (int32_t)vidx[e + S] : c0;
+                const uint32_t o0 = atomicAdd(pk + c0, dec);
+                const uint32_t o1 = two ? atomicAdd(pk + c1, dec) : 0u;
+                update(c0, f, o0);
+                if (two) update(c1, f, o1);
             }
         }
         __syncthreads();
@@ -835,11 +764,9 @@ DpgCompactPlace plan_dpg_compact(const fs_code *c) {
     p.pk = take(4 * (G + 1));
     p.cptr4 = take(4 * (G + 1));
     p.vptr = take(4 * (K + 1));
-    p.lvl_v = take(4 * (K + 1));
     p.front = take(2 * 2 * (K + 1));  // the two symbol lists
     p.next = p.touched = -1;
     p.deg = take(2 * (G + 1));
-    p.slots = take(2 * (int64_t)kSlotCap);
     p.vidx = take(2 * (c->e_con + 1));
     p.known = take(K + 1);
     p.ok = take(G + 1);
