@@ -294,33 +294,46 @@ __device__ int2 block_excl_scan2(int2 c, int2 *tot, int2 *s_w) {
     return make_int2(before.x + v.x - c.x, before.y + v.y - c.y);
 }
 
+// The compact form's view of its pairs after the walk, all in shared memory:
+// pair p decodes pf[p] at level plv[p] with the constraint whose winning
+// bid is still in best[pf[p]] (low 16 bits); level l's pairs are
+// lvo[l] .. lvo[l + 1] - 1. px / py / pz / lsb / lcb are scratch for
+// format_path (over arrays the walk no longer needs).
+struct CompactPairs {
+    const uint32_t *best;
+    const uint16_t *pf, *plv, *deg;
+    const int32_t *cptr4;
+    int32_t *lvo, *px, *py, *pz, *lsb, *lcb;
+};
+
 // After the walk of the compact form: the payload's records from the pair
 // list (levels are contiguous ranges of pairs, so the level-relative offsets
 // are differences of prefix sums over the whole list). Per pair x = padded
 // row length (its recipe), y = its segments of kRecipeSeg entries, z = 1 when
 // it has several (a multi-segment pair takes an accumulator). Writes
-// pair_rec, seg_pair, chunk_pair and level_tab exactly as emit_level does
-// level by level, and fills cur's totals and maxima for finish_dpg. The
-// workspace's front_a / front_b / touched arrays (unused by this form, each
-// at least n_con + 1 >= levels + 1 entries) hold each level's prefixes.
-__device__ void format_path(const DpgArgs &a, LevelCursor &cur, const int32_t *cptr4, int2 *s_w2,
-                            int *s_max, const uint16_t *deg) {
+// pair_rec, seg_pair, chunk_pair, level_tab and flow_pinfo exactly as
+// emit_level does level by level, and fills cur's totals and maxima for
+// finish_dpg. Reads only shared memory.
+__device__ void format_path(const DpgArgs &a, LevelCursor &cur, const CompactPairs &q, int2 *s_w2,
+                            int *s_max) {
     const int tid = threadIdx.x, T = blockDim.x;
     const int32_t P = cur.np, NL = cur.level;
+    auto g_of = [&](int32_t p) { return (int32_t)(q.best[q.pf[p]] & 0xffffu); };
     auto sizes = [&](int32_t g, int *x, int *y, int *z) {
-        *x = cptr4[g + 1] - cptr4[g];
+        *x = q.cptr4[g + 1] - q.cptr4[g];
         *y = (*x + kRecipeSeg - 1) / kRecipeSeg;
         *z = *y > 1 ? 1 : 0;
     };
     if (tid < 4) s_max[tid] = 0;
-    // A: prefixes in pair order, kept in pair_rec[2p + 1] until C
+    if (tid == 0) q.lvo[NL] = P;
+    // A: prefixes in pair order
     const int per = (P + T - 1) / T;
     const int p0 = min(P, tid * per), p1 = min(P, p0 + per);
     int2 cxy = make_int2(0, 0);
     int cz = 0;
     for (int32_t p = p0; p < p1; ++p) {
         int x, y, z;
-        sizes(a.pair_rec[2 * (size_t)p].y, &x, &y, &z);
+        sizes(g_of(p), &x, &y, &z);
         cxy.x += x;
         cxy.y += y;
         cz += z;
@@ -329,28 +342,34 @@ __device__ void format_path(const DpgArgs &a, LevelCursor &cur, const int32_t *c
     int2 oxy = block_excl_scan2(cxy, &txy, s_w2);
     int2 oz = block_excl_scan2(make_int2(cz, 0), &tz2, s_w2);
     for (int32_t p = p0; p < p1; ++p) {
-        const int4 r = a.pair_rec[2 * (size_t)p];
         int x, y, z;
-        sizes(r.y, &x, &y, &z);
-        a.pair_rec[2 * (size_t)p + 1] = make_int4(oxy.x, oxy.y, oz.x, r.z);
+        sizes(g_of(p), &x, &y, &z);
+        q.px[p] = oxy.x;
+        q.py[p] = oxy.y;
+        q.pz[p] = oz.x;
         oxy.x += x;
         oxy.y += y;
         oz.x += z;
     }
     __syncthreads();
-    // B: per level its first pair's prefixes, its totals, and its segment
-    // and chunk list bases (each level's lists start on multiples of 4)
+    // B: per level its totals, and its segment and chunk list bases (each
+    // level's lists start on multiples of 4)
     const int perl = (NL + T - 1) / T;
     const int l0 = min(NL, tid * perl), l1 = min(NL, l0 + perl);
+    auto level_sizes = [&](int32_t l, int32_t *first, int32_t *next, int *recipes, int *segs, int *multi) {
+        *first = q.lvo[l];
+        *next = q.lvo[l + 1];
+        const int nx = *next < P ? q.px[*next] : txy.x, ny = *next < P ? q.py[*next] : txy.y;
+        const int nz = *next < P ? q.pz[*next] : tz2.x;
+        *recipes = nx - q.px[*first];
+        *segs = ny - q.py[*first];
+        *multi = nz - q.pz[*first];
+    };
     int2 c4 = make_int2(0, 0);
     for (int32_t l = l0; l < l1; ++l) {
-        const int32_t first = a.level_off[l], next = l + 1 < NL ? a.level_off[l + 1] : P;
-        const int4 gf = a.pair_rec[2 * (size_t)first + 1];
-        const int4 gn = next < P ? a.pair_rec[2 * (size_t)next + 1] : make_int4(txy.x, txy.y, tz2.x, 0);
-        const int recipes = gn.x - gf.x, segs = gn.y - gf.y, multi = gn.z - gf.z;
-        a.front_a[l] = gf.x;
-        a.front_b[l] = gf.y;
-        a.touched[l] = gf.z;
+        int32_t first, next;
+        int recipes, segs, multi;
+        level_sizes(l, &first, &next, &recipes, &segs, &multi);
         c4.x += (segs + 3) & ~3;
         c4.y += ((recipes >> 2) + 3) & ~3;
         atomicMax(s_max + 0, next - first);
@@ -361,35 +380,31 @@ __device__ void format_path(const DpgArgs &a, LevelCursor &cur, const int32_t *c
     int2 t4;
     int2 base = block_excl_scan2(c4, &t4, s_w2);
     for (int32_t l = l0; l < l1; ++l) {
-        const int32_t first = a.level_off[l], next = l + 1 < NL ? a.level_off[l + 1] : P;
-        const int4 gf = a.pair_rec[2 * (size_t)first + 1];
-        const int4 gn = next < P ? a.pair_rec[2 * (size_t)next + 1] : make_int4(txy.x, txy.y, tz2.x, 0);
-        const int recipes = gn.x - gf.x, segs = gn.y - gf.y;
+        int32_t first, next;
+        int recipes, segs, multi;
+        level_sizes(l, &first, &next, &recipes, &segs, &multi);
         a.level_tab[2 * l] = make_int4(first, next - first, base.x, segs);
         a.level_tab[2 * l + 1] = make_int4(base.y, recipes >> 2, 0, 0);
+        q.lsb[l] = base.x;
+        q.lcb[l] = base.y;
         base.x += (segs + 3) & ~3;
         base.y += ((recipes >> 2) + 3) & ~3;
     }
     __syncthreads();
     // C: the records and the segment / chunk lists
     for (int32_t p = p0; p < p1; ++p) {
-        const int4 r = a.pair_rec[2 * (size_t)p];
-        const int4 gp = a.pair_rec[2 * (size_t)p + 1];
-        const int32_t l = r.z, first = a.level_off[l], i = p - first;
+        const int32_t l = q.plv[p], first = q.lvo[l], i = p - first;
+        const int32_t f = q.pf[p], g = g_of(p);
         int x, y, z;
-        sizes(r.y, &x, &y, &z);
-        const int ro = gp.x - a.front_a[l], so = gp.y - a.front_b[l];
-        const int mslot = z ? gp.z - a.touched[l] : -1;
-        const int4 lt0 = a.level_tab[2 * l], lt1 = a.level_tab[2 * l + 1];
-        a.pair_rec[2 * (size_t)p] = make_int4(r.x, r.y, ro, mslot);
-        a.pair_rec[2 * (size_t)p + 1] = make_int4(cptr4[r.y], x, so, y);
-        for (int k = 0; k < y; ++k) a.seg_pair[lt0.z + so + k] = i;
-        for (int k = 0; k < (x >> 2); ++k) a.chunk_pair[lt1.x + (ro >> 2) + k] = i;
-        if (a.flow_pinfo) a.flow_pinfo[p] = (uint32_t)l | ((uint32_t)deg[r.y] << 16);
-    }
-    if (tid == 0) {
-        cur.sb = t4.x;
-        cur.cb = t4.y;
+        sizes(g, &x, &y, &z);
+        const int ro = q.px[p] - q.px[first], so = q.py[p] - q.py[first];
+        const int mslot = z ? q.pz[p] - q.pz[first] : -1;
+        a.pair_rec[2 * (size_t)p] = make_int4(f, g, ro, mslot);
+        a.pair_rec[2 * (size_t)p + 1] = make_int4(q.cptr4[g], x, so, y);
+        const int32_t sb = q.lsb[l] + so, cb = q.lcb[l] + (ro >> 2);
+        for (int k = 0; k < y; ++k) a.seg_pair[sb + k] = i;
+        for (int k = 0; k < (x >> 2); ++k) a.chunk_pair[cb + k] = i;
+        if (a.flow_pinfo) a.flow_pinfo[p] = (uint32_t)l | ((uint32_t)q.deg[g] << 16);
     }
     __syncthreads();
     cur.maxp = s_max[0];
@@ -601,7 +616,13 @@ DpgPlace plan_dpg(const fs_code *c) {
 }
 
 struct DpgCompactPlace {
-    int32_t best, pk, front, next, touched, known, cptr4, vptr, vidx, ok, deg, bytes;
+    // through the walk and the formatting
+    int32_t best, cptr4, deg, known, pf, plv, lvo;
+    // the walk only
+    int32_t pk, vptr, front, vidx, ok;
+    // the formatting only, over the walk's arrays
+    int32_t px, py, pz, lsb, lcb;
+    int32_t bytes;
 };
 
 __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgCompactPlace &pl) {
@@ -624,6 +645,9 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
     uint16_t *vidx = reinterpret_cast<uint16_t *>(smem + pl.vidx);
     uint16_t *deg = reinterpret_cast<uint16_t *>(smem + pl.deg);
     uint8_t *ok = smem + pl.ok;
+    uint16_t *pf = reinterpret_cast<uint16_t *>(smem + pl.pf);    // [K + 1] f of pair p
+    uint16_t *plv = reinterpret_cast<uint16_t *>(smem + pl.plv);  // [K + 1] level of pair p
+    int32_t *lvo = reinterpret_cast<int32_t *>(smem + pl.lvo);    // [K + 2] first pair of level l
 
     // Constraint c, left with the one unknown f, bids key = (degree, c) for
     // it; the first bid for f lists f for the level.
@@ -671,22 +695,24 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
             __syncthreads();
             continue;
         }
-        // B: pairs of the level; their records for the payload are formatted
-        // after the walk (here only a stub {f, g, level, 0}), and f's level
-        // goes to the dataflow plan
+        // B: pairs of the level, kept in shared memory (f and level per pair;
+        // g stays in f's winning bid: a decoded symbol gets no further bid)
+        // for the payload's records, formatted after the walk; f's level goes
+        // to the dataflow plan
         for (int i = tid; i < nt; i += T) {
             const int32_t f = touched[i];
             const int32_t g = (int32_t)(best[f] & 0xffffu);
             const int32_t p = cur.np + i;
             a.pair_f[p] = f;
             a.pair_g[p] = g;
-            a.pair_rec[2 * (size_t)p] = make_int4(f, g, cur.level, 0);
             a.flow_lvl[f] = (uint16_t)cur.level;
-            best[f] = kE;
+            pf[p] = (uint16_t)f;
+            plv[p] = (uint16_t)cur.level;
             known[f] = 1;
         }
         if (tid == 0) {
             a.level_off[cur.level] = cur.np;
+            lvo[cur.level] = cur.np;
             s_nt[par ^ 1] = 0;  // the list the next level's bids fill
         }
         __syncthreads();
@@ -729,7 +755,19 @@ __device__ __forceinline__ void dpg_compact_body(const DpgArgs &a, const DpgComp
         cur.np += nt;
         ++cur.level;
     }
-    format_path(a, cur, cptr4, s_w2, s_max, deg);
+    CompactPairs q;
+    q.best = best;
+    q.pf = pf;
+    q.plv = plv;
+    q.deg = deg;
+    q.cptr4 = cptr4;
+    q.lvo = lvo;
+    q.px = reinterpret_cast<int32_t *>(smem + pl.px);
+    q.py = reinterpret_cast<int32_t *>(smem + pl.py);
+    q.pz = reinterpret_cast<int32_t *>(smem + pl.pz);
+    q.lsb = reinterpret_cast<int32_t *>(smem + pl.lsb);
+    q.lcb = reinterpret_cast<int32_t *>(smem + pl.lcb);
+    format_path(a, cur, q, s_w2, s_max);
     finish_dpg(a, cur, known, &s_cnt, &s_cnt_data);
     if (tid == 0 && a.flow_list) a.flow_hdr[kFlowHdrList] = 1;  // after finish_dpg's clear
 }
@@ -760,16 +798,30 @@ DpgCompactPlace plan_dpg_compact(const fs_code *c) {
         o = (o + bytes + 15) & ~(int64_t)15;
         return (int32_t)at;
     };
+    // through the walk and the formatting (levels <= pairs <= K)
     p.best = take(4 * (K + 1));
-    p.pk = take(4 * (G + 1));
     p.cptr4 = take(4 * (G + 1));
+    p.deg = take(2 * (G + 1));
+    p.known = take(K + 1);
+    p.pf = take(2 * (K + 1));
+    p.plv = take(2 * (K + 1));
+    p.lvo = take(4 * (K + 2));
+    const int64_t live = o;
+    // the walk only
+    p.pk = take(4 * (G + 1));
     p.vptr = take(4 * (K + 1));
     p.front = take(2 * 2 * (K + 1));  // the two symbol lists
-    p.next = p.touched = -1;
-    p.deg = take(2 * (G + 1));
     p.vidx = take(2 * (c->e_con + 1));
-    p.known = take(K + 1);
     p.ok = take(G + 1);
+    const int64_t walk = o;
+    // the formatting only, over the walk's arrays
+    o = live;
+    p.px = take(4 * (K + 1));
+    p.py = take(4 * (K + 1));
+    p.pz = take(4 * (K + 1));
+    p.lsb = take(4 * (K + 2));
+    p.lcb = take(4 * (K + 2));
+    o = std::max(o, walk);
     if (o > (int64_t)c->smem_optin - 1024) return p;
     p.bytes = (int32_t)o;
     return p;
