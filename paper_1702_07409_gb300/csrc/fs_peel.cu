@@ -195,15 +195,13 @@ struct LevelCursor {
     int scan_buf = 0;
 };
 
-// Step B of a level: writes the pairs i < nt (pair_of(i) gives f, g and the
-// adjacency count of f) and stores the level's totals in *s_len (read them
-// after the next block barrier). lvl_v (may be null) receives the
-// level-relative adjacency slot of each pair and the total at nt. Called by
-// every thread; only the warps holding pairs scan.
+// Step B of a level in the general form: writes the pairs i < nt (pair_of(i)
+// gives f and g) with their payload records, and stores the level's totals in
+// *s_len (read them after the next block barrier). Called by every thread;
+// only the warps holding pairs scan.
 template <typename PairOf>
 __device__ void emit_level(const DpgArgs &a, LevelCursor &cur, int nt, PairOf pair_of,
-                           const int32_t *cptr4, int32_t *lvl_v, int4 (*s_warp4)[32],
-                           int4 *s_len) {
+                           const int32_t *cptr4, int4 (*s_warp4)[32], int4 *s_len) {
     int4 len = make_int4(0, 0, 0, 0);
     const int32_t sb = cur.sb;
     for (int base = 0; base < nt; base += blockDim.x) {
@@ -212,15 +210,13 @@ __device__ void emit_level(const DpgArgs &a, LevelCursor &cur, int nt, PairOf pa
         cur.scan_buf ^= 1;
         if ((int)(threadIdx.x >> 5) >= nw) continue;
         const int i = base + threadIdx.x;
-        int4 cnt = make_int4(0, 0, 0, 0);  // recipe, segments, multi, adjacency
+        int4 cnt = make_int4(0, 0, 0, 0);  // recipe, segments, multi (w unused)
         int32_t f = -1, g = -1;
         if (i < nt) {
-            int32_t vdeg;
-            pair_of(i, &f, &g, &vdeg);
+            pair_of(i, &f, &g);
             cnt.x = cptr4[g + 1] - cptr4[g];  // padded row length (multiple of 4)
             cnt.y = (cnt.x + kRecipeSeg - 1) / kRecipeSeg;
             cnt.z = cnt.y > 1 ? 1 : 0;
-            cnt.w = vdeg;
         }
         int4 total;
         const int4 off = warps_excl_scan4(cnt, &total, s_warp4, buf, nw);
@@ -235,7 +231,6 @@ __device__ void emit_level(const DpgArgs &a, LevelCursor &cur, int nt, PairOf pa
             for (int k = 0; k < cnt.y; ++k) a.seg_pair[sb + so + k] = i;
             const int32_t c0 = cur.cb + ((len.x + off.x) >> 2);
             for (int k = 0; k < (cnt.x >> 2); ++k) a.chunk_pair[c0 + k] = i;
-            if (lvl_v) lvl_v[i] = len.w + off.w;
         }
         len.x += total.x;
         len.y += total.y;
@@ -246,7 +241,6 @@ __device__ void emit_level(const DpgArgs &a, LevelCursor &cur, int nt, PairOf pa
         a.level_off[cur.level] = cur.np;
         a.level_tab[2 * cur.level] = make_int4(cur.np, nt, sb, len.y);
         a.level_tab[2 * cur.level + 1] = make_int4(cur.cb, len.x >> 2, 0, 0);
-        if (lvl_v) lvl_v[nt] = len.w;
         *s_len = len;
     }
 }
@@ -539,12 +533,11 @@ __device__ __forceinline__ void dpg_body(const DpgArgs &a, const DpgPlace &pl) {
         // B: pairs of the level
         emit_level(
             a, cur, nt,
-            [&](int i, int32_t *f, int32_t *g, int32_t *vdeg) {
+            [&](int i, int32_t *f, int32_t *g) {
                 *f = touched[i];
                 *g = (int32_t)(best[*f] & 0xffffffffull);
-                *vdeg = 0;
             },
-            cptr4, nullptr, s_warp4, &s_len);
+            cptr4, s_warp4, &s_len);
         for (int i = tid; i < nt; i += T) {
             const int32_t f = touched[i];
             best[f] = kEmpty;
