@@ -118,7 +118,11 @@ fs_status fs_code_info(const fs_code *code, int32_t *b, int32_t *m, int32_t *n,
  *   FS_TUNE_DPG_COMPACT  1 (default): the decoding schedule runs with 16-bit
  *                        indices and the whole graph in shared memory when
  *                        the code has at most 65536 intermediates and
- *                        constraints; 0: the general form
+ *                        constraints, no constraint of 65536 or more
+ *                        members, and its graph and peeling state fit one
+ *                        CTA's shared memory (219 KB at 4224 intermediates,
+ *                        5528 constraints and 34799 edges); 0: the general
+ *                        form
  *   FS_TUNE_L2_HINTS     1: encode and payload peel mark the blocks they
  *                        gather again as evict-last in L2 and streamed data
  *                        as evict-first; 0 (default): plain loads and stores
