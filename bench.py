@@ -100,6 +100,25 @@ def barrier():
         dist.barrier()
 
 
+class NoGC:
+    """Python's garbage collector off inside a timed region (as timeit does):
+    a collection pause between two launches would leave the GPU idle and
+    count as step time. Collects once on entry, outside the timed work."""
+
+    def __enter__(self):
+        import gc
+        gc.collect()
+        self.was = gc.isenabled()
+        gc.disable()
+        return self
+
+    def __exit__(self, *exc):
+        import gc
+        if self.was:
+            gc.enable()
+        return False
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples taken while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -342,7 +361,7 @@ def run_gpu(args):
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with NoGC(), ClockSampler(local) as clk:
         t0.record()
         for i in range(K):
             st.step(args.warmup + i, evs[i])
@@ -362,10 +381,11 @@ def run_gpu(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
-    e0.record()
-    st.run_e2e([args.warmup + i for i in range(K)])
-    e1.record()
-    torch.cuda.synchronize()
+    with NoGC():
+        e0.record()
+        st.run_e2e([args.warmup + i for i in range(K)])
+        e1.record()
+        torch.cuda.synchronize()
     barrier()
     ms_e2e = reduce_max(e0.elapsed_time(e1), device) / K
     # the last step's read-back: the decoded data equal the uploaded data
